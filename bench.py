@@ -1,0 +1,425 @@
+"""Benchmark: Wilson-clover dslash HBM GB/s (fraction of the HBM roofline) and solve
+seconds to a true residual of 1e-10, mixed precision vs plain FP64.
+
+Workload: the 24^3x128 Wilson-clover lattice (c_sw = 1.0, kappa = 0.1350, random SU(3)
+links exp(i sigma H) with sigma = 0.5 followed by 3 APE-like smoothing steps, clover
+from the plaquette leaves; Schwarz blocks 4^4 with 6 MR steps). Synthetic, seeded
+inputs stand in for the paper's production configurations.
+
+A timed step is one application of the full clover operator M = Ahat - kappa D in the
+headline storage precision (FP32 storage, 12-real links). `value` is algorithmic
+bytes per application x applications / time. After the timed region the other
+precisions are timed the same way and the solves are run (not part of `value`).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun every rank runs the same workload on its own GPU (independent
+replicas, weak scaling); rank 0 prints one JSON line.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+DIMS = (24, 24, 24, 128)
+KAPPA, CSW, SIGMA, SMEAR = 0.1350, 1.0, 0.5, 3
+KAPPA_SOLVE = 0.124          # below the critical kappa of this smoothed field
+SEED_GAUGE, SEED_SRC = 2001, 2002
+BLOCK, MR_STEPS = (4, 4, 4, 4), 6
+
+# algorithmic bytes per lattice site of one full clover-operator application:
+# 4 links (forward; the backward ones belong to neighbours) + spinor in + spinor out + clover
+SITE_BYTES = {
+    "f64": 4 * 18 * 8 + 24 * 8 + 24 * 8 + 72 * 8,        # 1536 (18-real links)
+    "f32": 4 * 12 * 4 + 24 * 4 + 24 * 4 + 72 * 4,        # 672  (12-real links)
+    "f16": 4 * 12 * 2 + (48 + 4) * 2 + 72 * 2 + 4,       # 344  (12-real links, norms)
+}
+SITE_FLOPS = 1872
+PREC_ID = {"f64": 0, "f32": 1, "f16": 2}
+HEADLINE = "f32"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason sampling while the timed region runs."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        self.proc.terminate()
+        self.proc.wait()
+        self.f.close()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup():
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(world, v, device):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(world, v, device):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------- CPU oracle
+class OracleSample:
+    """The FP64 numpy oracle applying M at a fixed random sample of sites of the
+    24^3x128 workload (the oracle as it stands, single thread). Field generation and
+    the clover at the sampled sites are set-up, outside the timed applications."""
+
+    def __init__(self, n_sites, fields=None):
+        import numpy as np
+        import torch
+        from oracle import wilson
+        from oracle.lattice import all_coords
+        from paper_1109_2935_gb300 import synth
+        if fields is None:
+            dev = "cuda" if torch.cuda.is_available() else "cpu"
+            U = synth.wilson_gauge(DIMS, SIGMA, SMEAR, SEED_GAUGE, device=dev)
+            psi = synth.wilson_spinor(DIMS, SEED_SRC, device=dev)
+        else:
+            U, psi = fields
+        self.U = U.cpu().numpy()
+        self.psi = psi.cpu().numpy()
+        coords = all_coords(DIMS)
+        rng = np.random.default_rng(5)
+        self.sites = coords[rng.choice(len(coords), n_sites, replace=False)]
+        self.A = np.zeros((DIMS[3], DIMS[2], DIMS[1], DIMS[0], 12, 12), dtype=np.complex128)
+        s = self.sites
+        self.A[s[:, 3], s[:, 2], s[:, 1], s[:, 0]] = wilson.clover(self.U, CSW, sites=s)
+        self.n = n_sites
+
+    def step(self):
+        from oracle import wilson
+        t0 = time.perf_counter()
+        wilson.apply_M(self.U, self.A, KAPPA, self.psi, True, sites=self.sites)
+        return time.perf_counter() - t0
+
+
+def run_reference(args):
+    """--impl reference: the FP64 CPU oracle as the reference arm (rank 0 only)."""
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return 0
+    n_sites = 16384
+    orc = OracleSample(n_sites)
+    for _ in range(args.warmup):
+        orc.step()
+    times = [orc.step() for _ in range(args.steps)]
+    tot = sum(times)
+    value = SITE_BYTES["f64"] * n_sites * len(times) / tot / 1e9
+    sample = f"M at {n_sites} fixed random sites of 24^3x128 per step, FP64 numpy, 1 thread"
+    line = {
+        "impl": "reference",
+        "metric": "Wilson-clover dslash HBM GB/s (algorithmic bytes, % of HBM roofline); "
+                  "solve s to true resid 1e-10 vs plain FP64",
+        "value": value, "unit": "GB/s", "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "wilson-clover 24x24x24x128 csw=1.0 kappa=0.135 sigma=0.5 smear=3",
+                   "sample": sample},
+        "cpu_baseline": {"value": value, "unit": "GB/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------------------- GPU arm
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-solve", action="store_true", help="skip the solve section")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer e2e timing")
+    ap.add_argument("--dims", type=int, nargs=4, default=list(DIMS),
+                    help="lattice extents (profiling cases use a smaller lattice)")
+    ap.add_argument("--precs", default="f64,f32,f16", help="precisions to keep and time")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_1109_2935_gb300 import dirac, synth
+
+    dims = tuple(args.dims)
+    precs = [p for p in args.precs.split(",") if p in PREC_ID]
+    if HEADLINE not in precs:
+        precs.append(HEADLINE)
+    U = synth.wilson_gauge(dims, SIGMA, SMEAR, SEED_GAUGE, device=dev)
+    src = synth.wilson_spinor(dims, SEED_SRC, device=dev)
+    mask = sum(1 << PREC_ID[p] for p in precs) | 1  # FP64 kept for the solves
+    lat = dirac.Lattice(dims, dirac.WILSON_CLOVER, kappa=KAPPA, csw=CSW, block=BLOCK,
+                        mr_steps=MR_STEPS, recon=(18, 12, 12), prec_mask=mask)
+    lat.load_gauge(U)
+    V = lat.volume
+    stream = torch.cuda.current_stream(dev)
+    fields = {}
+    for name in precs:
+        pid = PREC_ID[name]
+        x = lat.to_device(src, pid)
+        y = lat.new_field(pid)
+        fields[name] = (x, y)
+    torch.cuda.synchronize()
+
+    def time_apply(name, steps, warmup):
+        x, y = fields[name]
+        pid = PREC_ID[name]
+        for _ in range(warmup):
+            lat.apply(y, x, dirac.PARITY_FULL, pid, stream)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+        barrier(world)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ev[0].record(stream)
+        for i in range(steps):
+            lat.apply(y, x, dirac.PARITY_FULL, pid, stream)
+            ev[i + 1].record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+        wall = time.perf_counter() - t0
+        per = [ev[i].elapsed_time(ev[i + 1]) for i in range(steps)]
+        return sum(per), per, wall
+
+    peak, peak_kind = _peaks()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    total_ms, per, wall = time_apply(HEADLINE, args.steps, args.warmup)
+    clk = clocks.stop()
+    total_ms_max = max_over_ranks(world, total_ms, dev)
+    bytes_per_launch = SITE_BYTES[HEADLINE] * V
+    value = sum_over_ranks(world, bytes_per_launch * args.steps, dev) / (total_ms_max / 1e3) / 1e9
+    avg_launch_ms = total_ms / args.steps
+    achieved = bytes_per_launch / (avg_launch_ms / 1e3) / 1e9
+
+    # other precisions, same protocol (not part of `value`)
+    per_prec = {}
+    for name in precs:
+        n = max(50, args.steps // 5) if name != "f64" else max(20, args.steps // 20)
+        tms, p, _ = time_apply(name, n, 5)
+        ms = tms / n
+        gbs = SITE_BYTES[name] * V / (ms / 1e3) / 1e9
+        per_prec[name] = {"ms": round(ms, 5), "alg_GBps": round(gbs, 1),
+                          "frac_of_hbm": round(gbs / peak, 4),
+                          "gflops": round(SITE_FLOPS * V / (ms / 1e3) / 1e9, 1)}
+
+    # e2e: through the C ABI with host (pinned) natural-layout buffers
+    e2e = None
+    if not args.no_e2e:
+        e2e = time_e2e(lat, dirac, src, fields, stream, args, world, dev, bytes_per_launch)
+
+    # solves (second half of the metric), timed separately
+    solves = None
+    if not args.no_solve and dims == DIMS:
+        solves = run_solves(dirac, synth, U, src, dev)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu and dims == DIMS:
+        orc = OracleSample(16384, (U, src))
+        orc.step()
+        ts = [orc.step() for _ in range(3)]
+        gbs = SITE_BYTES["f64"] * orc.n * len(ts) / sum(ts) / 1e9
+        cpu = {"value": round(gbs, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
+               "sample": f"FP64 numpy oracle, M at {orc.n} fixed random sites of 24^3x128, "
+                         f"3 applications ({sum(ts):.2f} s), FP64 1536 B/site count"}
+    workload = "wilson-clover %dx%dx%dx%d csw=1.0 kappa=0.135 sigma=0.5 smear=3" % dims
+    return finish(args, world, rank, dev, value, total_ms_max, achieved, peak, peak_kind,
+                  bytes_per_launch, per_prec, clk, e2e, cpu, solves, wall, workload, V)
+
+
+def time_e2e(lat, dirac, src, fields, stream, args, world, dev, bytes_per_launch):
+    import torch
+    V = lat.volume
+    nat_in = torch.view_as_real(src.cpu()).contiguous().pin_memory()
+    nat_out = torch.empty_like(nat_in).pin_memory()
+    x, y = fields[HEADLINE]
+    pid = PREC_ID[HEADLINE]
+    sptr = stream.cuda_stream
+    e2e_steps = max(5, min(20, args.steps // 50))
+
+    def e2e_step():
+        dirac.dirac_import_spinor(lat.ctx, x.data_ptr(), pid, -1, nat_in.data_ptr(), 0, sptr)
+        dirac.dirac_apply(lat.ctx, y.data_ptr(), x.data_ptr(), -1, pid, sptr)
+        dirac.dirac_export_spinor(lat.ctx, nat_out.data_ptr(), 0, y.data_ptr(), pid, -1, sptr)
+
+    for _ in range(3):
+        e2e_step()
+    torch.cuda.synchronize()
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_s = max_over_ranks(world, time.perf_counter() - t0, dev)
+    e2e_value = sum_over_ranks(world, bytes_per_launch * e2e_steps, dev) / e2e_s / 1e9
+    nat_bytes = V * 24 * 8
+    return {"value": round(e2e_value, 3), "unit": "GB/s", "h2d_bytes_per_step": nat_bytes,
+            "d2h_bytes_per_step": nat_bytes, "steps": e2e_steps}
+
+
+def finish(args, world, rank, dev, value, total_ms_max, achieved, peak, peak_kind,
+           bytes_per_launch, per_prec, clk, e2e, cpu, solves, wall, workload, V):
+    if rank == 0:
+        line = {
+            "metric": "Wilson-clover dslash HBM GB/s (algorithmic bytes, % of HBM roofline); "
+                      "solve s to true resid 1e-10 vs plain FP64",
+            "value": round(value, 2), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(total_ms_max / args.steps, 5),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": workload,
+                       "op": "full clover M, FP32 storage, 12-real links",
+                       "global_batch": world, "parallelism": f"replicas{world}",
+                       "l2": "inputs (1.19 GB per application) larger than L2, no flush"},
+            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
+                         "unit": "GB/s", "frac": round(achieved / peak, 4),
+                         "peak_kind": peak_kind, "traffic": None,
+                         "kernel": "wilson_kernel<P32,12,full>",
+                         "bytes_per_launch": bytes_per_launch},
+            "per_precision": per_prec,
+            "clocks": clk,
+            "e2e": e2e,
+            "gpu_launches": args.steps,
+            "cpu_baseline": cpu,
+            "solve": solves,
+            "wall_s_timed": round(wall, 4),
+        }
+        traffic = _traffic_from_profile()
+        if traffic:
+            line["roofline"]["traffic"] = traffic
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def _traffic_from_profile():
+    """DRAM bytes per launch of the headline kernel from the committed ncu summary,
+    if it records one for the current kernel."""
+    p = os.path.join(ROOT, "profiles", "wilson_clover_M_f32_24x24x24x128.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return d.get("dram_bytes_per_launch")
+    except Exception:
+        return None
+
+
+def run_solves(dirac, synth, U, src, dev):
+    """Mixed-precision vs plain-FP64 solves on the same 24^3x128 field."""
+    import torch
+    out = {}
+    for kappa, tag, budget in ((KAPPA_SOLVE, "kappa_0.124", 4000), (KAPPA, "kappa_0.135", 600)):
+        lat = dirac.Lattice(DIMS, dirac.WILSON_CLOVER, kappa=kappa, csw=CSW, block=BLOCK,
+                            mr_steps=MR_STEPS, recon=(18, 12, 12))
+        lat.load_gauge(U)
+        b = lat.to_device(src, dirac.F64)
+        x = lat.new_field(dirac.F64)
+        res = {}
+        runs = [("gcr_dd_mixed", dirac.GCR_DD, dirac.F16, dirac.F16, 0.1),
+                ("gcr_dd_f64", dirac.GCR_DD, dirac.F64, dirac.F64, 0.0),
+                ("bicgstab_mixed", dirac.BICGSTAB, dirac.F16, dirac.F16, 0.1),
+                ("bicgstab_f64", dirac.BICGSTAB, dirac.F64, dirac.F64, 0.0)]
+        for name, alg, sp, pp, delta in runs:
+            if kappa == KAPPA and name.endswith("f64"):
+                continue
+            torch.cuda.synchronize()
+            st = lat.solve(x, b, alg, tol=1e-10, max_iter=budget if alg != dirac.GCR_DD else budget // 4,
+                           k_max=16, delta=delta, prec_sloppy=sp, prec_precond=pp, raise_on_error=False)
+            res[name] = {k: (round(v, 6) if isinstance(v, float) else v) for k, v in st.items()}
+        for alg in ("gcr_dd", "bicgstab"):
+            a, b_ = res.get(f"{alg}_mixed"), res.get(f"{alg}_f64")
+            if a and b_ and a["status"] == "OK" and b_["status"] == "OK":
+                res[f"{alg}_speedup_vs_f64"] = round(b_["seconds"] / a["seconds"], 3)
+        out[tag] = res
+        lat.close()
+    return out
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,184 @@
+/*
+ * dirac.h -- C ABI of libdirac, a single-GPU (sm_103a) implementation of the solver
+ * hot path of "Scaling Lattice QCD beyond 100 GPUs" (Babich et al., SC11):
+ * the Wilson-clover and improved-staggered (asqtad) Dirac operators, the
+ * non-overlapping additive Schwarz preconditioner, and the Krylov solvers around
+ * them (CG, BiCGstab, mixed-precision GCR-DD of Algorithm 1).
+ *
+ * Problem statement (Sec. 2.1, Eq. 1): solve M x = b for a large sparse M.
+ *
+ * General rules
+ *  - Every function returns an int status: DIRAC_OK (0) or a negative DIRAC_ERR_*.
+ *    No function aborts, exits or throws across this boundary. After an error,
+ *    dirac_last_error(ctx) holds a one-line description.
+ *  - All GPU work is enqueued on the stream argument (a cudaStream_t passed as
+ *    void*; NULL means the legacy default stream). Functions that return host
+ *    values (reductions, solve) synchronise that stream before returning.
+ *  - Spinor arguments are CALLER-OWNED DEVICE POINTERS in the library's device
+ *    layout (below); sizes come from dirac_field_bytes(). Input and output of one
+ *    call must not alias. Gauge and clover fields are copied into library-owned
+ *    device storage by dirac_load_gauge and live until dirac_destroy.
+ *  - One context is used by one host thread at a time.
+ *
+ * Natural (host-application) layout, FP64, x fastest and t slowest (Sec. 6.2):
+ *    links   [t][z][y][x][mu][3][3][re,im]     mu = 0,1,2,3 = x,y,z,t
+ *    Wilson spinor    [t][z][y][x][spin 4][colour 3][re,im]
+ *    staggered spinor [t][z][y][x][colour 3][re,im]
+ *
+ * Device layout of a spinor field (Sec. 5: fields reordered for coalescing;
+ * Sec. 6.1 / Fig. 2: Vh = V/2 sites per parity):
+ *    a parity half-field holds the Vh sites of one parity in checkerboard order
+ *    cb = lex/2 (lex = ((t*LZ + z)*LY + y)*LX + x, parity = (x+y+z+t) mod 2);
+ *    it is an array of 16-byte (F64 Wilson/staggered, F32 Wilson, F16 Wilson),
+ *    8-byte (F32 staggered) or 4-byte (F16 staggered) chunks, chunk-major:
+ *    chunk k of site cb sits at  base + (k*Vh + cb) * chunk_bytes,
+ *    and the reals of a site are ordered (spin, colour, re/im). F16 fields hold
+ *    binary16 values of v/n followed by Vh FP32 per-site norms n = max|v|.
+ *    A full field is the even half-field followed by the odd half-field.
+ */
+#ifndef DIRAC_H
+#define DIRAC_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dirac_ctx dirac_ctx;
+
+enum {
+  DIRAC_OK = 0,
+  DIRAC_ERR_ARG = -1,           /* invalid argument (sizes, enums, null pointers) */
+  DIRAC_ERR_CUDA = -2,          /* a CUDA call failed; the message names it */
+  DIRAC_ERR_OOM = -3,           /* device allocation failed */
+  DIRAC_ERR_UNSUPPORTED = -4,   /* operation not defined for this operator/precision */
+  DIRAC_ERR_NOT_CONVERGED = -5, /* max_iter reached; x holds the last iterate */
+  DIRAC_ERR_BREAKDOWN = -6,     /* a Krylov denominator vanished */
+  DIRAC_ERR_NONFINITE = -7,     /* NaN/Inf in a residual norm */
+  DIRAC_ERR_TIMEOUT = -8,       /* reserved: a bounded device wait ran out */
+  DIRAC_ERR_STATE = -9          /* e.g. apply before the gauge field was loaded */
+};
+
+typedef enum { DIRAC_WILSON_CLOVER = 0, DIRAC_ASQTAD = 1 } dirac_kind;
+typedef enum { DIRAC_PREC_F64 = 0, DIRAC_PREC_F32 = 1, DIRAC_PREC_F16 = 2 } dirac_prec;
+/* Gauge compression, Sec. 5 strategy (a): reals stored per SU(3) link. */
+typedef enum { DIRAC_RECON_18 = 18, DIRAC_RECON_12 = 12, DIRAC_RECON_8 = 8 } dirac_recon;
+/* Output parity: FULL = whole lattice, EVEN/ODD = one checkerboard. */
+typedef enum { DIRAC_PARITY_FULL = -1, DIRAC_PARITY_EVEN = 0, DIRAC_PARITY_ODD = 1 } dirac_parity;
+
+typedef struct {
+  int dims[4];          /* LX, LY, LZ, LT: each even, >= 2 */
+  int t_antiperiodic;   /* 1: fermion hops across the t boundary get a factor -1 */
+  dirac_kind kind;
+  double kappa;         /* Wilson-clover hopping parameter, kappa = 1/(2(4+m)) (Eq. 2) */
+  double csw;           /* clover coefficient; 0 = plain Wilson */
+  double mass;          /* asqtad mass m (Eq. 3) */
+  int block[4];         /* Schwarz block extents; each divides dims; block volume <= 512 */
+  int mr_steps;         /* minimal-residual steps per block solve (Sec. 8.1) */
+  int recon[3];         /* dirac_recon per precision F64/F32/F16 for the Wilson links and
+                           the asqtad long links (fat links are always 18: not unitary) */
+  unsigned prec_mask;   /* bit p set: keep the operator in precision p (0 = all three) */
+} dirac_params;
+
+/* Create a context for one lattice. Allocates the library-owned gauge/clover storage
+ * lazily at dirac_load_gauge. Returns DIRAC_ERR_ARG for odd or non-positive dims,
+ * blocks that do not tile the lattice, or unknown enums. */
+int dirac_create(const dirac_params* params, dirac_ctx** out);
+int dirac_destroy(dirac_ctx* ctx);
+const char* dirac_last_error(const dirac_ctx* ctx);
+
+/* Bytes of one spinor field in the device layout for precision/parity. */
+size_t dirac_field_bytes(const dirac_ctx* ctx, dirac_prec prec, dirac_parity parity);
+
+/* Load a gauge field given in the natural FP64 layout (host or device memory,
+ * on_device = 0/1) and convert it on the GPU into every precision of prec_mask with
+ * that precision's compression. which = 0: Wilson links U (also builds the clover
+ * term A of Eq. 2 from the plaquette leaves, and stores 1 + 2 kappa A); 1: asqtad fat
+ * links; 2: asqtad long links (Eq. 3). The caller keeps ownership of `links`. */
+int dirac_load_gauge(dirac_ctx* ctx, const double* links, int which, int on_device, void* stream);
+
+/* Convert a spinor between the natural FP64 layout (host or device) and the device
+ * layout of precision `prec`. For a parity half-field only the sites of that parity
+ * are read (import) or written (export); the natural array always spans the lattice. */
+int dirac_import_spinor(dirac_ctx* ctx, void* dst, dirac_prec prec, dirac_parity parity,
+                        const double* src_natural, int src_on_device, void* stream);
+int dirac_export_spinor(dirac_ctx* ctx, double* dst_natural, int dst_on_device,
+                        const void* src, dirac_prec prec, dirac_parity parity, void* stream);
+
+/* out = M in (Eq. 2 in kappa form M = 1 + 2 kappa A - kappa D; Eq. 3 M = m - D/2) on
+ * full fields when parity == FULL. With parity EVEN/ODD: out_p = D_{p,1-p} in_{1-p},
+ * the hopping block of D alone (half-fields in and out). `in` and `out` are device
+ * fields of precision `prec`; the operator runs in that precision. */
+int dirac_apply(dirac_ctx* ctx, void* out, const void* in, dirac_parity parity, dirac_prec prec,
+                void* stream);
+/* Same with the adjoint: Wilson gamma5 M gamma5 (projectors swapped), asqtad m + D/2
+ * (parity form: D^dagger = -D). */
+int dirac_apply_dagger(dirac_ctx* ctx, void* out, const void* in, dirac_parity parity,
+                       dirac_prec prec, void* stream);
+/* Normal operator M^dagger M. FULL: whole lattice (both kinds). EVEN/ODD: asqtad
+ * only, (M^dagger M)_pp = m^2 - 1/4 D_{p,1-p} D_{1-p,p} on a half-field (Sec. 3.1:
+ * the staggered normal matrix decouples the parities). */
+int dirac_apply_normal(dirac_ctx* ctx, void* out, const void* in, dirac_parity parity,
+                       dirac_prec prec, void* stream);
+
+/* out = K in: the non-overlapping additive Schwarz preconditioner of Sec. 3.2 / 8.1
+ * for the Wilson-clover operator. On every block (params.block) the operator with
+ * Dirichlet (zero) block boundaries is solved by params.mr_steps minimal-residual
+ * steps from x = 0, with block-local inner products. Full fields of precision
+ * `prec`. DIRAC_ERR_UNSUPPORTED for asqtad. */
+int schwarz_precondition(dirac_ctx* ctx, void* out, const void* in, dirac_prec prec, void* stream);
+
+/* BLAS-1 on device fields (Sec. 6.1: contiguous fields make BLAS and reductions
+ * straightforward). All accumulate in FP64; results are returned to host memory
+ * after a stream synchronisation. dot = sum conj(x_i) y_i. */
+int dirac_norm2(dirac_ctx* ctx, const void* x, dirac_prec prec, dirac_parity parity,
+                double* result, void* stream);
+int dirac_cdot(dirac_ctx* ctx, const void* x, const void* y, dirac_prec prec,
+               dirac_parity parity, double result[2], void* stream);
+/* y += a x, then result = ||y||^2 (a complex: a_re + i a_im). */
+int dirac_caxpy_norm(dirac_ctx* ctx, double a_re, double a_im, const void* x, void* y,
+                     dirac_prec prec, dirac_parity parity, double* result, void* stream);
+/* dst (precision dprec) = src (precision sprec), element-wise with re-encoding. */
+int dirac_convert(dirac_ctx* ctx, void* dst, dirac_prec dprec, const void* src, dirac_prec sprec,
+                  dirac_parity parity, void* stream);
+
+typedef enum {
+  DIRAC_SOLVER_CG_NORMAL = 0,      /* CG on M^dagger M x = b, full lattice (Sec. 3.1) */
+  DIRAC_SOLVER_CG_EVEN_NORMAL = 1, /* CG on (M^dagger M)_ee x_e = b_e, asqtad (Sec. 3.1) */
+  DIRAC_SOLVER_BICGSTAB = 2,       /* BiCGstab on M x = b, Wilson-clover (Sec. 3.1) */
+  DIRAC_SOLVER_GCR_DD = 3,         /* GCR with the Schwarz preconditioner (Algorithm 1) */
+  DIRAC_SOLVER_GCR = 4             /* GCR of Algorithm 1 with K = 1 */
+} dirac_solver;
+
+typedef struct {
+  dirac_solver alg;
+  double tol;           /* target ||b - A x|| / ||b|| of the solved system, in FP64 */
+  int max_iter;         /* Krylov iterations (GCR: preconditioned directions) */
+  int k_max;            /* GCR Krylov subspace size (Algorithm 1) */
+  double delta;         /* GCR: restart when ||r_k||/||r_0|| < delta (0 = off);
+                           CG/BiCGstab: reliable update when ||r|| < delta * max ||r||
+                           since the last update (0 = pure, no updates) */
+  int use_x0;           /* 1: x holds the initial guess on entry */
+  dirac_prec prec_sloppy;  /* precision of the Krylov vectors and the inner operator */
+  dirac_prec prec_precond; /* precision of the Schwarz preconditioner (GCR_DD) */
+} dirac_solver_params;
+
+typedef struct {
+  int iters, restarts, reliable_updates, dslash_calls, precond_calls;
+  double true_rel_resid;   /* final ||b - A x|| / ||b|| recomputed in FP64 */
+  double seconds;          /* wall time of the solve including the final sync */
+  double flops;            /* operator + BLAS flops by the counts in the design doc */
+} dirac_solver_stats;
+
+/* Solve A x = b in FP64 (A = M, M^dagger M or (M^dagger M)_ee per alg). x and b are
+ * caller-owned FP64 device fields (full fields, or EVEN half-fields for
+ * CG_EVEN_NORMAL). Returns DIRAC_OK when the FP64 true residual meets tol,
+ * DIRAC_ERR_NOT_CONVERGED when max_iter ran out (x = last iterate, stats filled). */
+int solve(dirac_ctx* ctx, void* x, const void* b, const dirac_solver_params* params,
+          dirac_solver_stats* stats, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DIRAC_H */

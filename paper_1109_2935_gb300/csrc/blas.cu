@@ -1,0 +1,453 @@
+// BLAS-1 and global reductions on spinor fields (Sec. 6.1: fields stored
+// contiguously so that BLAS-like routines and global reductions run efficiently;
+// Sec. 8.2: this linear algebra is bandwidth-bound).
+//
+// Every kernel works site by site on fields of any storage precision (FP64, FP32,
+// FP16 + per-site norm). Arithmetic is FP32 when no FP64 field takes part and FP64
+// otherwise; every reduction accumulates in FP64. Reductions are deterministic:
+// each block writes a partial sum, the last block to finish adds the partials in a
+// fixed order and writes the result into mapped pinned host memory.
+#include <cstring>
+#include <string>
+
+#include "internal.h"
+
+namespace dirac {
+
+static constexpr int kRedBlocks = 152 * 4;
+static constexpr int kThreads = 256;
+static constexpr int kMaxMulti = 16;
+
+struct Blas {
+  double* partials = nullptr;  // device [kRedBlocks][3]
+  unsigned* ticket = nullptr;  // device counter, returns to 0 after each reduction
+  double* host_res = nullptr;  // pinned, mapped
+  double* dev_res = nullptr;   // device alias of host_res
+  std::string err;
+};
+
+Blas* blas_create() {
+  Blas* b = new Blas();
+  if (cudaMalloc(&b->partials, sizeof(double) * 3 * kRedBlocks) != cudaSuccess ||
+      cudaMalloc(&b->ticket, sizeof(unsigned)) != cudaSuccess ||
+      cudaMemset(b->ticket, 0, sizeof(unsigned)) != cudaSuccess ||
+      cudaHostAlloc(&b->host_res, sizeof(double) * 4, cudaHostAllocMapped) != cudaSuccess ||
+      cudaHostGetDevicePointer(&b->dev_res, b->host_res, 0) != cudaSuccess) {
+    blas_destroy(b);
+    return nullptr;
+  }
+  return b;
+}
+
+void blas_destroy(Blas* b) {
+  if (!b) return;
+  if (b->partials) cudaFree(b->partials);
+  if (b->ticket) cudaFree(b->ticket);
+  if (b->host_res) cudaFreeHost(b->host_res);
+  delete b;
+}
+
+const char* blas_error(Blas* b) { return b ? b->err.c_str() : "no blas context"; }
+
+// ---------------------------------------------------------------- site access
+template <int NR, typename T>
+__device__ __forceinline__ void site_load(const FieldRef& f, int s, T v[NR]) {
+  int q = s >= f.Vh ? 1 : 0;
+  int cb = s - q * f.Vh;
+  const char* b = f.p + q * f.hb;
+  if (f.prec == P64) {
+    double t[NR];
+    SpinorIO<P64, NR>::template load<false>(b, f.Vh, cb, t);
+#pragma unroll
+    for (int k = 0; k < NR; ++k) v[k] = (T)t[k];
+  } else if (f.prec == P32) {
+    float t[NR];
+    SpinorIO<P32, NR>::template load<false>(b, f.Vh, cb, t);
+#pragma unroll
+    for (int k = 0; k < NR; ++k) v[k] = (T)t[k];
+  } else {
+    float t[NR];
+    SpinorIO<P16, NR>::template load<false>(b, f.Vh, cb, t);
+#pragma unroll
+    for (int k = 0; k < NR; ++k) v[k] = (T)t[k];
+  }
+}
+
+template <int NR, typename T>
+__device__ __forceinline__ void site_store(const FieldRef& f, int s, const T v[NR]) {
+  int q = s >= f.Vh ? 1 : 0;
+  int cb = s - q * f.Vh;
+  char* b = f.p + q * f.hb;
+  if (f.prec == P64) {
+    double t[NR];
+#pragma unroll
+    for (int k = 0; k < NR; ++k) t[k] = (double)v[k];
+    SpinorIO<P64, NR>::store(b, f.Vh, cb, t);
+  } else {
+    float t[NR];
+#pragma unroll
+    for (int k = 0; k < NR; ++k) t[k] = (float)v[k];
+    if (f.prec == P32) SpinorIO<P32, NR>::store(b, f.Vh, cb, t);
+    else SpinorIO<P16, NR>::store(b, f.Vh, cb, t);
+  }
+}
+
+// ---------------------------------------------------------------- operations
+// Each op: void operator()(int site, double acc[3]) const.
+template <int NR, typename T> struct OpCopy {
+  FieldRef d, s;
+  __device__ void operator()(int i, double*) const { T v[NR]; site_load<NR>(s, i, v); site_store<NR>(d, i, v); }
+};
+template <int NR, typename T> struct OpZero {
+  FieldRef x;
+  __device__ void operator()(int i, double*) const {
+    T v[NR];
+#pragma unroll
+    for (int k = 0; k < NR; ++k) v[k] = 0;
+    site_store<NR>(x, i, v);
+  }
+};
+// y = a x + b y
+template <int NR, typename T> struct OpAxpby {
+  FieldRef x, y; T ar, ai, br, bi;
+  __device__ void operator()(int i, double*) const {
+    T u[NR], v[NR];
+    site_load<NR>(x, i, u); site_load<NR>(y, i, v);
+#pragma unroll
+    for (int k = 0; k < NR / 2; ++k) {
+      T xr = u[2 * k], xi = u[2 * k + 1], yr = v[2 * k], yi = v[2 * k + 1];
+      v[2 * k] = ar * xr - ai * xi + br * yr - bi * yi;
+      v[2 * k + 1] = ar * xi + ai * xr + br * yi + bi * yr;
+    }
+    site_store<NR>(y, i, v);
+  }
+};
+// z = x + a y
+template <int NR, typename T> struct OpXpayTo {
+  FieldRef x, y, z; T ar, ai;
+  __device__ void operator()(int i, double*) const {
+    T u[NR], v[NR];
+    site_load<NR>(x, i, u); site_load<NR>(y, i, v);
+#pragma unroll
+    for (int k = 0; k < NR / 2; ++k) {
+      T yr = v[2 * k], yi = v[2 * k + 1];
+      u[2 * k] += ar * yr - ai * yi;
+      u[2 * k + 1] += ar * yi + ai * yr;
+    }
+    site_store<NR>(z, i, u);
+  }
+};
+// y += a x + b z
+template <int NR, typename T> struct OpAxpbzAdd {
+  FieldRef x, z, y; T ar, ai, br, bi;
+  __device__ void operator()(int i, double*) const {
+    T u[NR], w[NR], v[NR];
+    site_load<NR>(x, i, u); site_load<NR>(z, i, w); site_load<NR>(y, i, v);
+#pragma unroll
+    for (int k = 0; k < NR / 2; ++k) {
+      v[2 * k] += ar * u[2 * k] - ai * u[2 * k + 1] + br * w[2 * k] - bi * w[2 * k + 1];
+      v[2 * k + 1] += ar * u[2 * k + 1] + ai * u[2 * k] + br * w[2 * k + 1] + bi * w[2 * k];
+    }
+    site_store<NR>(y, i, v);
+  }
+};
+template <int NR, typename T> struct OpNorm2 {
+  FieldRef x;
+  __device__ void operator()(int i, double* acc) const {
+    T u[NR];
+    site_load<NR>(x, i, u);
+    T s = 0;
+#pragma unroll
+    for (int k = 0; k < NR; ++k) s = fma(u[k], u[k], s);
+    acc[0] += (double)s;
+  }
+};
+// (x, y) and ||x||^2
+template <int NR, typename T> struct OpCdotNorm {
+  FieldRef x, y;
+  __device__ void operator()(int i, double* acc) const {
+    T u[NR], v[NR];
+    site_load<NR>(x, i, u); site_load<NR>(y, i, v);
+    T re = 0, im = 0, nn = 0;
+#pragma unroll
+    for (int k = 0; k < NR / 2; ++k) {
+      T xr = u[2 * k], xi = u[2 * k + 1], yr = v[2 * k], yi = v[2 * k + 1];
+      re = fma(xr, yr, re); re = fma(xi, yi, re);
+      im = fma(xr, yi, im); im = fma(-xi, yr, im);
+      nn = fma(xr, xr, nn); nn = fma(xi, xi, nn);
+    }
+    acc[0] += (double)re; acc[1] += (double)im; acc[2] += (double)nn;
+  }
+};
+// y += a x ; ||y||^2, (w, y)
+template <int NR, typename T, bool DOT> struct OpCaxpyNorm {
+  FieldRef x, y, w; T ar, ai;
+  __device__ void operator()(int i, double* acc) const {
+    T u[NR], v[NR];
+    site_load<NR>(x, i, u); site_load<NR>(y, i, v);
+#pragma unroll
+    for (int k = 0; k < NR / 2; ++k) {
+      T xr = u[2 * k], xi = u[2 * k + 1];
+      v[2 * k] += ar * xr - ai * xi;
+      v[2 * k + 1] += ar * xi + ai * xr;
+    }
+    site_store<NR>(y, i, v);
+    if (y.prec == P16) site_load<NR>(y, i, v);  // reduce what is stored
+    T nn = 0;
+#pragma unroll
+    for (int k = 0; k < NR; ++k) nn = fma(v[k], v[k], nn);
+    acc[0] += (double)nn;
+    if (DOT) {
+      T ww[NR], re = 0, im = 0;
+      site_load<NR>(w, i, ww);
+#pragma unroll
+      for (int k = 0; k < NR / 2; ++k) {
+        re = fma(ww[2 * k], v[2 * k], re); re = fma(ww[2 * k + 1], v[2 * k + 1], re);
+        im = fma(ww[2 * k], v[2 * k + 1], im); im = fma(-ww[2 * k + 1], v[2 * k], im);
+      }
+      acc[1] += (double)re; acc[2] += (double)im;
+    }
+  }
+};
+// x *= s ; (x, y)
+template <int NR, typename T> struct OpScaleCdot {
+  FieldRef x, y; T s;
+  __device__ void operator()(int i, double* acc) const {
+    T u[NR], v[NR];
+    site_load<NR>(x, i, u);
+#pragma unroll
+    for (int k = 0; k < NR; ++k) u[k] *= s;
+    site_store<NR>(x, i, u);
+    if (x.prec == P16) site_load<NR>(x, i, u);
+    site_load<NR>(y, i, v);
+    T re = 0, im = 0;
+#pragma unroll
+    for (int k = 0; k < NR / 2; ++k) {
+      re = fma(u[2 * k], v[2 * k], re); re = fma(u[2 * k + 1], v[2 * k + 1], re);
+      im = fma(u[2 * k], v[2 * k + 1], im); im = fma(-u[2 * k + 1], v[2 * k], im);
+    }
+    acc[0] += (double)re; acc[1] += (double)im;
+  }
+};
+// y = b - y ; ||y||^2
+template <int NR, typename T> struct OpXmyNorm {
+  FieldRef b, y;
+  __device__ void operator()(int i, double* acc) const {
+    T u[NR], v[NR];
+    site_load<NR>(b, i, u); site_load<NR>(y, i, v);
+    T nn = 0;
+#pragma unroll
+    for (int k = 0; k < NR; ++k) {
+      v[k] = u[k] - v[k];
+      nn = fma(v[k], v[k], nn);
+    }
+    site_store<NR>(y, i, v);
+    acc[0] += (double)nn;
+  }
+};
+struct MultiCoef { FieldRef x[kMaxMulti]; double cr[kMaxMulti], ci[kMaxMulti]; int n; };
+template <int NR, typename T> struct OpMultiCaxpy {
+  MultiCoef m; FieldRef y;
+  __device__ void operator()(int i, double*) const {
+    T v[NR];
+    site_load<NR>(y, i, v);
+    for (int j = 0; j < m.n; ++j) {
+      T u[NR];
+      site_load<NR>(m.x[j], i, u);
+      const T cr = (T)m.cr[j], ci = (T)m.ci[j];
+#pragma unroll
+      for (int k = 0; k < NR / 2; ++k) {
+        v[2 * k] += cr * u[2 * k] - ci * u[2 * k + 1];
+        v[2 * k + 1] += cr * u[2 * k + 1] + ci * u[2 * k];
+      }
+    }
+    site_store<NR>(y, i, v);
+  }
+};
+
+// ---------------------------------------------------------------- kernels
+template <class Op>
+__global__ void __launch_bounds__(kThreads) map_kernel(Op op, int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) op(i, nullptr);
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block sum of three values; the result is valid in thread 0.
+__device__ __forceinline__ void block_sum3(double acc[3], double (*sh)[3]) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) acc[k] = warp_sum(acc[k]);
+  if (lane == 0)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) sh[warp][k] = acc[k];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < 3; ++k) {
+      double s = 0;
+      for (int w = 0; w < kThreads / 32; ++w) s += sh[w][k];
+      acc[k] = s;
+    }
+  }
+  __syncthreads();
+}
+
+template <class Op>
+__global__ void __launch_bounds__(kThreads) reduce_kernel(Op op, int n, double* partials,
+                                                          unsigned* ticket, double* res) {
+  __shared__ double sh[kThreads / 32][3];
+  __shared__ bool last;
+  double acc[3] = {0, 0, 0};
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) op(i, acc);
+  block_sum3(acc, sh);
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < 3; ++k) partials[3 * blockIdx.x + k] = acc[k];
+    __threadfence();
+    unsigned t = atomicAdd(ticket, 1u);
+    last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double s[3] = {0, 0, 0};
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) s[k] += __ldcg(partials + 3 * b + k);
+  block_sum3(s, sh);
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < 3; ++k) res[k] = s[k];
+    *ticket = 0;
+  }
+}
+
+// ---------------------------------------------------------------- host dispatch
+static int nsites(const FieldRef& f) { return f.npar * f.Vh; }
+
+static bool any64(std::initializer_list<const FieldRef*> fs) {
+  for (auto f : fs) if (f->prec == P64) return true;
+  return false;
+}
+
+static int check(Blas* b, const char* what) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    b->err = std::string(what) + ": " + cudaGetErrorString(e);
+    return DIRAC_ERR_CUDA;
+  }
+  return DIRAC_OK;
+}
+
+template <class Op>
+static int run_map(Blas* b, const Op& op, int n, cudaStream_t st) {
+  int grid = (n + kThreads - 1) / kThreads;
+  if (grid > 152 * 16) grid = 152 * 16;
+  if (grid < 1) grid = 1;
+  map_kernel<Op><<<grid, kThreads, 0, st>>>(op, n);
+  return check(b, "blas map kernel");
+}
+
+template <class Op>
+static int run_reduce(Blas* b, const Op& op, int n, double* out, int nout, cudaStream_t st) {
+  int grid = (n + kThreads - 1) / kThreads;
+  if (grid > kRedBlocks) grid = kRedBlocks;
+  if (grid < 1) grid = 1;
+  reduce_kernel<Op><<<grid, kThreads, 0, st>>>(op, n, b->partials, b->ticket, b->dev_res);
+  int rc = check(b, "blas reduce kernel");
+  if (rc) return rc;
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    b->err = std::string("reduction sync: ") + cudaGetErrorString(e);
+    return DIRAC_ERR_CUDA;
+  }
+  for (int k = 0; k < nout; ++k) out[k] = ((volatile double*)b->host_res)[k];
+  return DIRAC_OK;
+}
+
+// Dispatch on (reals per site, arithmetic type).
+#define DISPATCH(nr, dbl, BODY)                               \
+  do {                                                        \
+    if ((nr) == 24) {                                         \
+      constexpr int NR = 24;                                  \
+      if (dbl) { using T = double; BODY; } else { using T = float; BODY; } \
+    } else {                                                  \
+      constexpr int NR = 6;                                   \
+      if (dbl) { using T = double; BODY; } else { using T = float; BODY; } \
+    }                                                         \
+  } while (0)
+
+int blas_copy(Blas* b, const FieldRef& dst, const FieldRef& src, cudaStream_t st) {
+  DISPATCH(dst.nr, any64({&dst, &src}), return run_map(b, (OpCopy<NR, T>{dst, src}), nsites(dst), st));
+}
+int blas_zero(Blas* b, const FieldRef& x, cudaStream_t st) {
+  if (cudaMemsetAsync(x.p, 0, x.hb * x.npar, st) != cudaSuccess) return check(b, "memset");
+  return DIRAC_OK;
+}
+int blas_axpby(Blas* b, double ar, double ai, const FieldRef& x, double br, double bi,
+               const FieldRef& y, cudaStream_t st) {
+  DISPATCH(y.nr, any64({&x, &y}),
+           return run_map(b, (OpAxpby<NR, T>{x, y, (T)ar, (T)ai, (T)br, (T)bi}), nsites(y), st));
+}
+int blas_xpay_to(Blas* b, const FieldRef& x, double ar, double ai, const FieldRef& y,
+                 const FieldRef& z, cudaStream_t st) {
+  DISPATCH(z.nr, any64({&x, &y, &z}),
+           return run_map(b, (OpXpayTo<NR, T>{x, y, z, (T)ar, (T)ai}), nsites(z), st));
+}
+int blas_axpbz_add(Blas* b, double ar, double ai, const FieldRef& x, double br, double bi,
+                   const FieldRef& z, const FieldRef& y, cudaStream_t st) {
+  DISPATCH(y.nr, any64({&x, &z, &y}),
+           return run_map(b, (OpAxpbzAdd<NR, T>{x, z, y, (T)ar, (T)ai, (T)br, (T)bi}), nsites(y), st));
+}
+int blas_norm2(Blas* b, const FieldRef& x, double* out, cudaStream_t st) {
+  DISPATCH(x.nr, any64({&x}), return run_reduce(b, (OpNorm2<NR, T>{x}), nsites(x), out, 1, st));
+}
+int blas_cdot(Blas* b, const FieldRef& x, const FieldRef& y, double out[2], cudaStream_t st) {
+  DISPATCH(x.nr, any64({&x, &y}),
+           return run_reduce(b, (OpCdotNorm<NR, T>{x, y}), nsites(x), out, 2, st));
+}
+int blas_cdot_norm(Blas* b, const FieldRef& x, const FieldRef& y, double out[3], cudaStream_t st) {
+  DISPATCH(x.nr, any64({&x, &y}),
+           return run_reduce(b, (OpCdotNorm<NR, T>{x, y}), nsites(x), out, 3, st));
+}
+int blas_caxpy_norm(Blas* b, double ar, double ai, const FieldRef& x, const FieldRef& y,
+                    double* out, cudaStream_t st) {
+  DISPATCH(y.nr, any64({&x, &y}),
+           return run_reduce(b, (OpCaxpyNorm<NR, T, false>{x, y, y, (T)ar, (T)ai}), nsites(y), out, 1, st));
+}
+int blas_caxpy_norm_dot(Blas* b, double ar, double ai, const FieldRef& x, const FieldRef& y,
+                        const FieldRef& w, double out[3], cudaStream_t st) {
+  DISPATCH(y.nr, any64({&x, &y, &w}),
+           return run_reduce(b, (OpCaxpyNorm<NR, T, true>{x, y, w, (T)ar, (T)ai}), nsites(y), out, 3, st));
+}
+int blas_scale_cdot(Blas* b, double s, const FieldRef& x, const FieldRef& y, double out[2],
+                    cudaStream_t st) {
+  DISPATCH(x.nr, any64({&x, &y}),
+           return run_reduce(b, (OpScaleCdot<NR, T>{x, y, (T)s}), nsites(x), out, 2, st));
+}
+int blas_xmy_norm(Blas* b, const FieldRef& bb, const FieldRef& y, double* out, cudaStream_t st) {
+  DISPATCH(y.nr, any64({&bb, &y}),
+           return run_reduce(b, (OpXmyNorm<NR, T>{bb, y}), nsites(y), out, 1, st));
+}
+int blas_multi_caxpy(Blas* b, int n, const double* cr, const double* ci, const FieldRef* xs,
+                     const FieldRef& y, cudaStream_t st) {
+  for (int j0 = 0; j0 < n; j0 += kMaxMulti) {
+    MultiCoef m;
+    m.n = n - j0 < kMaxMulti ? n - j0 : kMaxMulti;
+    bool dbl = y.prec == P64;
+    for (int j = 0; j < m.n; ++j) {
+      m.x[j] = xs[j0 + j];
+      m.cr[j] = cr[j0 + j];
+      m.ci[j] = ci[j0 + j];
+      dbl = dbl || xs[j0 + j].prec == P64;
+    }
+    int rc;
+    DISPATCH(y.nr, dbl, rc = run_map(b, (OpMultiCaxpy<NR, T>{m, y}), nsites(y), st));
+    if (rc) return rc;
+  }
+  return DIRAC_OK;
+}
+
+}  // namespace dirac

@@ -1,0 +1,235 @@
+// Wilson-clover stencil (Eq. 2), one thread per output site.
+//
+//   hopping term  D psi(x) = sum_mu [ (1 - gamma_mu) U_mu(x) psi(x+mu)
+//                                     + (1 + gamma_mu) U_mu(x-mu)^dagger psi(x-mu) ]
+//   kappa form    M psi    = Ahat psi - kappa D psi,  Ahat = 1 + 2 kappa A  (stored)
+//   adjoint       M^dagger = Ahat - kappa D^dagger, D^dagger swaps the projectors.
+//
+// Spin basis: chiral, gamma_mu = [[0, B_mu], [B_mu^dagger, 0]] with
+//   B_x = [[0, i], [i, 0]], B_y = [[0, -1], [1, 0]], B_z = [[i, 0], [0, -i]], B_t = 1.
+// For P = 1 + s gamma_mu (s = -1 forward, +1 backward; flipped for the adjoint):
+//   P psi = [h ; s B^dagger h]  with  h = psi_up + s B psi_low,
+// so every hop multiplies only the 2-spin half spinor h by the link (Sec. 5:
+// "similarity transforms to increase the sparsity of the Dirac matrices").
+#pragma once
+#include "field.cuh"
+
+namespace dirac {
+
+struct WilsonArg {
+  char* out[2];          // output half-field base for each parity
+  const char* in[2];     // input half-field base for each parity
+  const char* gauge;     // links of this precision, [mu][parity][chunk][Vh]
+  const char* clover;    // Ahat of this precision, [parity][chunk][Vh]; null: Ahat = 1
+  Geom g;
+  double kappa;
+  int dagger;            // 1: apply the adjoint
+  int out_parity;        // hop mode: parity of the output half-field
+};
+
+template <int MU, typename T>
+__device__ __forceinline__ void wilson_hop(C<T> acc[4][3], const T* psi, const Link<T>& U,
+                                           bool link_dag, T s, T bc) {
+  C<T> h0[3], h1[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    C<T> u0 = {psi[2 * c], psi[2 * c + 1]};
+    C<T> u1 = {psi[6 + 2 * c], psi[6 + 2 * c + 1]};
+    C<T> l0 = {psi[12 + 2 * c], psi[12 + 2 * c + 1]};
+    C<T> l1 = {psi[18 + 2 * c], psi[18 + 2 * c + 1]};
+    if (MU == 0) {        // B l = (i l1, i l0)
+      h0[c] = u0 + s * times_i(l1);
+      h1[c] = u1 + s * times_i(l0);
+    } else if (MU == 1) { // B l = (-l1, l0)
+      h0[c] = u0 - s * l1;
+      h1[c] = u1 + s * l0;
+    } else if (MU == 2) { // B l = (i l0, -i l1)
+      h0[c] = u0 + s * times_i(l0);
+      h1[c] = u1 - s * times_i(l1);
+    } else {              // B l = l
+      h0[c] = u0 + s * l0;
+      h1[c] = u1 + s * l1;
+    }
+    h0[c] = bc * h0[c];
+    h1[c] = bc * h1[c];
+  }
+  C<T> v0[3], v1[3];
+  if (link_dag) {
+    su3_mv_dag(U, h0, v0);
+    su3_mv_dag(U, h1, v1);
+  } else {
+    su3_mv(U, h0, v0);
+    su3_mv(U, h1, v1);
+  }
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    acc[0][c] = acc[0][c] + v0[c];
+    acc[1][c] = acc[1][c] + v1[c];
+    if (MU == 0) {        // B^dagger v = (-i v1, -i v0)
+      acc[2][c] = acc[2][c] - s * times_i(v1[c]);
+      acc[3][c] = acc[3][c] - s * times_i(v0[c]);
+    } else if (MU == 1) { // B^dagger v = (v1, -v0)
+      acc[2][c] = acc[2][c] + s * v1[c];
+      acc[3][c] = acc[3][c] - s * v0[c];
+    } else if (MU == 2) { // B^dagger v = (-i v0, i v1)
+      acc[2][c] = acc[2][c] - s * times_i(v0[c]);
+      acc[3][c] = acc[3][c] + s * times_i(v1[c]);
+    } else {
+      acc[2][c] = acc[2][c] + s * v0[c];
+      acc[3][c] = acc[3][c] + s * v1[c];
+    }
+  }
+}
+
+// out[12] = Ahat(x) in[12] for the clover of precision PREC (block by block to bound
+// register use).
+template <int PREC, typename T>
+__device__ __forceinline__ void apply_clover_site(const char* b, int Vh, int cb, const C<T> in[12],
+                                                  C<T> out[12]) {
+  if constexpr (PREC == P64) {
+#pragma unroll
+    for (int blk = 0; blk < 2; ++blk) {
+      double v[36];
+#pragma unroll
+      for (int k = 0; k < 18; ++k) {
+        double2 q = ldg_chunk<double2>(b + ((size_t)(18 * blk + k) * Vh + cb) * 16);
+        v[2 * k] = q.x; v[2 * k + 1] = q.y;
+      }
+      herm6_mv<T>(v, in + 6 * blk, out + 6 * blk);
+    }
+  } else if constexpr (PREC == P32) {
+#pragma unroll
+    for (int blk = 0; blk < 2; ++blk) {
+      float v[36];
+#pragma unroll
+      for (int k = 0; k < 9; ++k) {
+        float4 q = ldg_chunk<float4>(b + ((size_t)(9 * blk + k) * Vh + cb) * 16);
+        v[4 * k] = q.x; v[4 * k + 1] = q.y; v[4 * k + 2] = q.z; v[4 * k + 3] = q.w;
+      }
+      herm6_mv<T>(v, in + 6 * blk, out + 6 * blk);
+    }
+  } else {
+    float v[72];
+    CloverIO<P16>::load(b, Vh, cb, v);
+    herm6_mv<T>(v, in, out);
+    herm6_mv<T>(v + 36, in + 6, out + 6);
+  }
+}
+
+template <int PREC, int R, bool FULLM>
+__global__ void __launch_bounds__(128) wilson_kernel(const WilsonArg a) {
+  using T = typename Real<PREC>::T;
+  const Geom& g = a.g;
+  const int Vh = g.Vh;
+  int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  int par, cb;
+  if (FULLM) {
+    if (idx >= 2 * Vh) return;
+    par = idx >= Vh;
+    cb = idx - par * Vh;
+  } else {
+    if (idx >= Vh) return;
+    par = a.out_parity;
+    cb = idx;
+  }
+  int x[4];
+  cb_coords(g, cb, par, x);
+  const char* src = a.in[1 - par];
+  const T sf = a.dagger ? (T)1 : (T)-1;  // forward projector 1 - gamma (adjoint: 1 + gamma)
+  const T sb = -sf;
+
+  C<T> acc[4][3];
+#pragma unroll
+  for (int s = 0; s < 4; ++s)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) acc[s][c] = C<T>{0, 0};
+
+#pragma unroll
+  for (int mu = 0; mu < 4; ++mu) {
+    // forward neighbour x + mu, link U_mu(x) stored at (mu, par, cb)
+    {
+      int y[4] = {x[0], x[1], x[2], x[3]};
+      T bc = 1;
+      if (++y[mu] == g.L[mu]) {
+        y[mu] = 0;
+        if (mu == 3 && g.apbc) bc = -1;
+      }
+      T psi[24];
+      SpinorIO<PREC, 24>::load(src, Vh, cb_index(g, y), psi);
+      Link<T> U;
+      LinkIO<PREC, R>::load(a.gauge, Vh, mu, par, cb, U);
+      if (mu == 0) wilson_hop<0>(acc, psi, U, false, sf, bc);
+      if (mu == 1) wilson_hop<1>(acc, psi, U, false, sf, bc);
+      if (mu == 2) wilson_hop<2>(acc, psi, U, false, sf, bc);
+      if (mu == 3) wilson_hop<3>(acc, psi, U, false, sf, bc);
+    }
+    // backward neighbour x - mu, link U_mu(x - mu) stored at (mu, 1 - par, cb(x - mu))
+    {
+      int y[4] = {x[0], x[1], x[2], x[3]};
+      T bc = 1;
+      if (y[mu]-- == 0) {
+        y[mu] = g.L[mu] - 1;
+        if (mu == 3 && g.apbc) bc = -1;
+      }
+      int ycb = cb_index(g, y);
+      T psi[24];
+      SpinorIO<PREC, 24>::load(src, Vh, ycb, psi);
+      Link<T> U;
+      LinkIO<PREC, R>::load(a.gauge, Vh, mu, 1 - par, ycb, U);
+      if (mu == 0) wilson_hop<0>(acc, psi, U, true, sb, bc);
+      if (mu == 1) wilson_hop<1>(acc, psi, U, true, sb, bc);
+      if (mu == 2) wilson_hop<2>(acc, psi, U, true, sb, bc);
+      if (mu == 3) wilson_hop<3>(acc, psi, U, true, sb, bc);
+    }
+  }
+
+  T out[24];
+  if (FULLM) {
+    T self[24];
+    SpinorIO<PREC, 24>::load(a.in[par], Vh, cb, self);
+    C<T> sv[12], av[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) sv[k] = C<T>{self[2 * k], self[2 * k + 1]};
+    if (a.clover) {
+      apply_clover_site<PREC, T>(a.clover + (size_t)par * CloverIO<PREC>::parity_bytes(Vh), Vh, cb, sv, av);
+    } else {
+#pragma unroll
+      for (int k = 0; k < 12; ++k) av[k] = sv[k];
+    }
+    const T mk = -(T)a.kappa;
+#pragma unroll
+    for (int s = 0; s < 4; ++s)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        out[6 * s + 2 * c] = fma(mk, acc[s][c].r, av[3 * s + c].r);
+        out[6 * s + 2 * c + 1] = fma(mk, acc[s][c].i, av[3 * s + c].i);
+      }
+  } else {
+#pragma unroll
+    for (int s = 0; s < 4; ++s)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        out[6 * s + 2 * c] = acc[s][c].r;
+        out[6 * s + 2 * c + 1] = acc[s][c].i;
+      }
+  }
+  SpinorIO<PREC, 24>::store(a.out[par], Vh, cb, out);
+}
+
+template <int PREC>
+void launch_wilson_prec(int recon, bool fullm, const WilsonArg& a, cudaStream_t st) {
+  int n = fullm ? 2 * a.g.Vh : a.g.Vh;
+  dim3 block(128), grid((n + 127) / 128);
+  if (recon == 18) {
+    if (fullm) wilson_kernel<PREC, 18, true><<<grid, block, 0, st>>>(a);
+    else wilson_kernel<PREC, 18, false><<<grid, block, 0, st>>>(a);
+  } else if (recon == 12) {
+    if (fullm) wilson_kernel<PREC, 12, true><<<grid, block, 0, st>>>(a);
+    else wilson_kernel<PREC, 12, false><<<grid, block, 0, st>>>(a);
+  } else {
+    if (fullm) wilson_kernel<PREC, 8, true><<<grid, block, 0, st>>>(a);
+    else wilson_kernel<PREC, 8, false><<<grid, block, 0, st>>>(a);
+  }
+}
+
+}  // namespace dirac

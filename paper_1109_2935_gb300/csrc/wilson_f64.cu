@@ -1,0 +1,9 @@
+// Wilson-clover stencil instantiations for P64 storage (kernel template in wilson.cuh).
+#include "wilson.cuh"
+#include "internal.h"
+
+namespace dirac {
+void launch_wilson_p64(int recon, bool fullm, const WilsonArg& a, cudaStream_t st) {
+  launch_wilson_prec<P64>(recon, fullm, a, st);
+}
+}  // namespace dirac

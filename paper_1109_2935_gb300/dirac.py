@@ -1,0 +1,246 @@
+"""Thin ctypes binding of libdirac (C ABI in include/dirac.h).
+
+The functions here carry the C names and only marshal arguments: every operator,
+preconditioner, BLAS and solver step runs in the CUDA library. There is no Python or
+CPU fallback: importing this module fails loudly when ``libdirac.so`` has not been
+built (``python -m paper_1109_2935_gb300.build``).
+
+Spinor arguments are device pointers (ints, e.g. ``tensor.data_ptr()``) in the
+library's device layout; ``Lattice`` below wraps a context and accepts torch tensors.
+"""
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libdirac.so")
+
+OK = 0
+ERR_ARG, ERR_CUDA, ERR_OOM, ERR_UNSUPPORTED = -1, -2, -3, -4
+ERR_NOT_CONVERGED, ERR_BREAKDOWN, ERR_NONFINITE, ERR_TIMEOUT, ERR_STATE = -5, -6, -7, -8, -9
+ERR_NAMES = {0: "OK", -1: "ERR_ARG", -2: "ERR_CUDA", -3: "ERR_OOM", -4: "ERR_UNSUPPORTED",
+             -5: "ERR_NOT_CONVERGED", -6: "ERR_BREAKDOWN", -7: "ERR_NONFINITE",
+             -8: "ERR_TIMEOUT", -9: "ERR_STATE"}
+
+WILSON_CLOVER, ASQTAD = 0, 1
+F64, F32, F16 = 0, 1, 2
+PARITY_FULL, PARITY_EVEN, PARITY_ODD = -1, 0, 1
+CG_NORMAL, CG_EVEN_NORMAL, BICGSTAB, GCR_DD, GCR = 0, 1, 2, 3, 4
+
+
+class DiracParams(ctypes.Structure):
+    _fields_ = [("dims", ctypes.c_int * 4), ("t_antiperiodic", ctypes.c_int),
+                ("kind", ctypes.c_int), ("kappa", ctypes.c_double), ("csw", ctypes.c_double),
+                ("mass", ctypes.c_double), ("block", ctypes.c_int * 4), ("mr_steps", ctypes.c_int),
+                ("recon", ctypes.c_int * 3), ("prec_mask", ctypes.c_uint)]
+
+
+class SolverParams(ctypes.Structure):
+    _fields_ = [("alg", ctypes.c_int), ("tol", ctypes.c_double), ("max_iter", ctypes.c_int),
+                ("k_max", ctypes.c_int), ("delta", ctypes.c_double), ("use_x0", ctypes.c_int),
+                ("prec_sloppy", ctypes.c_int), ("prec_precond", ctypes.c_int)]
+
+
+class SolverStats(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("restarts", ctypes.c_int),
+                ("reliable_updates", ctypes.c_int), ("dslash_calls", ctypes.c_int),
+                ("precond_calls", ctypes.c_int), ("true_rel_resid", ctypes.c_double),
+                ("seconds", ctypes.c_double), ("flops", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"libdirac.so is not built ({LIB_PATH}); run "
+                      "`python -m paper_1109_2935_gb300.build`")
+lib = ctypes.CDLL(LIB_PATH)
+
+_vp, _ci, _cd, _sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_size_t
+_pd = ctypes.POINTER(ctypes.c_double)
+_SIGS = {
+    "dirac_create": (_ci, [ctypes.POINTER(DiracParams), ctypes.POINTER(_vp)]),
+    "dirac_destroy": (_ci, [_vp]),
+    "dirac_last_error": (ctypes.c_char_p, [_vp]),
+    "dirac_field_bytes": (_sz, [_vp, _ci, _ci]),
+    "dirac_load_gauge": (_ci, [_vp, _vp, _ci, _ci, _vp]),
+    "dirac_import_spinor": (_ci, [_vp, _vp, _ci, _ci, _vp, _ci, _vp]),
+    "dirac_export_spinor": (_ci, [_vp, _vp, _ci, _vp, _ci, _ci, _vp]),
+    "dirac_apply": (_ci, [_vp, _vp, _vp, _ci, _ci, _vp]),
+    "dirac_apply_dagger": (_ci, [_vp, _vp, _vp, _ci, _ci, _vp]),
+    "dirac_apply_normal": (_ci, [_vp, _vp, _vp, _ci, _ci, _vp]),
+    "schwarz_precondition": (_ci, [_vp, _vp, _vp, _ci, _vp]),
+    "dirac_norm2": (_ci, [_vp, _vp, _ci, _ci, _pd, _vp]),
+    "dirac_cdot": (_ci, [_vp, _vp, _vp, _ci, _ci, _pd, _vp]),
+    "dirac_caxpy_norm": (_ci, [_vp, _cd, _cd, _vp, _vp, _ci, _ci, _pd, _vp]),
+    "dirac_convert": (_ci, [_vp, _vp, _ci, _vp, _ci, _ci, _vp]),
+    "solve": (_ci, [_vp, _vp, _vp, ctypes.POINTER(SolverParams), ctypes.POINTER(SolverStats), _vp]),
+}
+EXPORTED = tuple(_SIGS)
+for _name, (_res, _args) in _SIGS.items():
+    _f = getattr(lib, _name)
+    _f.restype, _f.argtypes = _res, _args
+    globals()[_name] = _f
+
+
+class DiracError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERR_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return stream if isinstance(stream, int) else stream.cuda_stream
+
+
+class Lattice:
+    """A libdirac context plus torch-tensor marshalling. Owns nothing but the context."""
+
+    def __init__(self, dims, kind=WILSON_CLOVER, kappa=0.12, csw=0.0, mass=0.0,
+                 t_antiperiodic=True, block=None, mr_steps=6, recon=(18, 12, 12),
+                 prec_mask=7):
+        if block is None:  # largest of 4, 2, 1 dividing each extent
+            block = tuple(next(b for b in (4, 2, 1) if d % b == 0) for d in dims)
+        p = DiracParams()
+        p.dims[:] = list(dims)
+        p.t_antiperiodic = int(t_antiperiodic)
+        p.kind = kind
+        p.kappa, p.csw, p.mass = kappa, csw, mass
+        p.block[:] = list(block)
+        p.mr_steps = mr_steps
+        p.recon[:] = list(recon)
+        p.prec_mask = prec_mask
+        self.params = p
+        self.dims = tuple(dims)
+        self.kind = kind
+        self.nr = 24 if kind == WILSON_CLOVER else 6
+        h = _vp()
+        rc = dirac_create(ctypes.byref(p), ctypes.byref(h))
+        if rc != OK:
+            raise DiracError(rc, "dirac_create rejected the parameters")
+        self.ctx = h
+
+    def close(self):
+        if self.ctx:
+            dirac_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def check(self, rc, what):
+        if rc != OK:
+            raise DiracError(rc, f"{what}: {dirac_last_error(self.ctx).decode()}")
+        return rc
+
+    @property
+    def volume(self):
+        v = 1
+        for d in self.dims:
+            v *= d
+        return v
+
+    def field_bytes(self, prec, parity=PARITY_FULL):
+        return dirac_field_bytes(self.ctx, prec, parity)
+
+    def new_field(self, prec, parity=PARITY_FULL, device="cuda"):
+        import torch
+        return torch.zeros(self.field_bytes(prec, parity), dtype=torch.uint8, device=device)
+
+    def load_gauge(self, links, which=0, stream=None):
+        """links: complex128 [t,z,y,x,mu,3,3] tensor (CPU or CUDA), natural layout."""
+        import torch
+        t = torch.view_as_real(links.contiguous()) if links.is_complex() else links.contiguous()
+        on_dev = int(t.is_cuda)
+        self.check(dirac_load_gauge(self.ctx, t.data_ptr(), which, on_dev, _stream(stream)),
+                   "dirac_load_gauge")
+        if not on_dev:
+            torch.cuda.synchronize()
+
+    def import_spinor(self, dst, prec, parity, natural, stream=None):
+        import torch
+        t = torch.view_as_real(natural.contiguous()) if natural.is_complex() else natural.contiguous()
+        self.check(dirac_import_spinor(self.ctx, dst.data_ptr(), prec, parity, t.data_ptr(),
+                                       int(t.is_cuda), _stream(stream)), "dirac_import_spinor")
+        return dst
+
+    def export_spinor(self, src, prec, parity, natural, stream=None):
+        """natural: complex128 tensor to fill (CPU or CUDA)."""
+        import torch
+        t = torch.view_as_real(natural)
+        self.check(dirac_export_spinor(self.ctx, t.data_ptr(), int(t.is_cuda), src.data_ptr(),
+                                       prec, parity, _stream(stream)), "dirac_export_spinor")
+        return natural
+
+    def natural_shape(self):
+        LX, LY, LZ, LT = self.dims
+        return (LT, LZ, LY, LX, 4, 3) if self.nr == 24 else (LT, LZ, LY, LX, 3)
+
+    def to_device(self, natural, prec, parity=PARITY_FULL):
+        f = self.new_field(prec, parity)
+        return self.import_spinor(f, prec, parity, natural)
+
+    def to_natural(self, field, prec, parity=PARITY_FULL, device="cuda"):
+        import torch
+        out = torch.zeros(self.natural_shape(), dtype=torch.complex128, device=device)
+        self.export_spinor(field, prec, parity, out)
+        if device != "cuda":
+            torch.cuda.synchronize()
+        return out
+
+    def apply(self, out, inp, parity=PARITY_FULL, prec=F64, stream=None):
+        return self.check(dirac_apply(self.ctx, out.data_ptr(), inp.data_ptr(), parity, prec,
+                                      _stream(stream)), "dirac_apply")
+
+    def apply_dagger(self, out, inp, parity=PARITY_FULL, prec=F64, stream=None):
+        return self.check(dirac_apply_dagger(self.ctx, out.data_ptr(), inp.data_ptr(), parity,
+                                             prec, _stream(stream)), "dirac_apply_dagger")
+
+    def apply_normal(self, out, inp, parity=PARITY_FULL, prec=F64, stream=None):
+        return self.check(dirac_apply_normal(self.ctx, out.data_ptr(), inp.data_ptr(), parity,
+                                             prec, _stream(stream)), "dirac_apply_normal")
+
+    def schwarz(self, out, inp, prec=F16, stream=None):
+        return self.check(schwarz_precondition(self.ctx, out.data_ptr(), inp.data_ptr(), prec,
+                                               _stream(stream)), "schwarz_precondition")
+
+    def norm2(self, x, prec, parity=PARITY_FULL, stream=None):
+        r = ctypes.c_double()
+        self.check(dirac_norm2(self.ctx, x.data_ptr(), prec, parity, ctypes.byref(r),
+                               _stream(stream)), "dirac_norm2")
+        return r.value
+
+    def cdot(self, x, y, prec, parity=PARITY_FULL, stream=None):
+        r = (ctypes.c_double * 2)()
+        self.check(dirac_cdot(self.ctx, x.data_ptr(), y.data_ptr(), prec, parity, r,
+                              _stream(stream)), "dirac_cdot")
+        return complex(r[0], r[1])
+
+    def caxpy_norm(self, a, x, y, prec, parity=PARITY_FULL, stream=None):
+        r = ctypes.c_double()
+        a = complex(a)
+        self.check(dirac_caxpy_norm(self.ctx, a.real, a.imag, x.data_ptr(), y.data_ptr(), prec,
+                                    parity, ctypes.byref(r), _stream(stream)), "dirac_caxpy_norm")
+        return r.value
+
+    def convert(self, dst, dprec, src, sprec, parity=PARITY_FULL, stream=None):
+        return self.check(dirac_convert(self.ctx, dst.data_ptr(), dprec, src.data_ptr(), sprec,
+                                        parity, _stream(stream)), "dirac_convert")
+
+    def solve(self, x, b, alg, tol=1e-10, max_iter=10000, k_max=16, delta=0.0, use_x0=False,
+              prec_sloppy=F64, prec_precond=F64, stream=None, raise_on_error=True):
+        sp = SolverParams(alg, tol, max_iter, k_max, delta, int(use_x0), prec_sloppy, prec_precond)
+        st = SolverStats()
+        rc = solve(self.ctx, x.data_ptr(), b.data_ptr(), ctypes.byref(sp), ctypes.byref(st),
+                   _stream(stream))
+        if raise_on_error and rc != OK:
+            raise DiracError(rc, f"solve: {dirac_last_error(self.ctx).decode()} "
+                                 f"(stats {st.as_dict()})")
+        d = st.as_dict()
+        d["status"] = ERR_NAMES.get(rc, rc)
+        return d

@@ -17,3 +17,15 @@ def pytest_configure(config):
 def rng():
     import numpy as np
     return np.random.default_rng(12345)
+
+
+@pytest.fixture(scope="session")
+def dirac():
+    """The built libdirac binding (GPU tests only)."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1109_2935_gb300 import build
+    build.build()
+    from paper_1109_2935_gb300 import dirac as d
+    return d

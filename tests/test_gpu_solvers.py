@@ -1,0 +1,127 @@
+"""GPU solves (CG, BiCGstab, GCR, GCR-DD of Algorithm 1) judged by the FP64 oracle:
+the oracle recomputes ||b - A x|| / ||b|| from the exported solution, which must be
+<= the requested tolerance (1e-10), in pure FP64 and in mixed precision."""
+import numpy as np
+import pytest
+
+from helpers import F16, F32, F64
+from oracle import staggered, wilson
+from oracle import solvers as osolv
+from paper_1109_2935_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _oracle_resid(A, x, b):
+    r = b - A(x)
+    return np.linalg.norm(r) / np.linalg.norm(b)
+
+
+@pytest.mark.parametrize("sloppy,delta", [(F64, 0.0), (F32, 0.1), (F16, 0.1)])
+def test_cg_normal_4444(dirac, sloppy, delta):
+    """4^4 plain Wilson (kappa = 0.12, sigma = 0.3, antiperiodic t): CG on
+    M^dagger M x = b to 1e-10, and the same solution as the oracle's CG."""
+    dims = (4, 4, 4, 4)
+    U = synth.wilson_gauge(dims, 0.3, 0, 1001)
+    b = synth.wilson_spinor(dims, 1002)
+    lat = dirac.Lattice(dims, dirac.WILSON_CLOVER, kappa=0.12, csw=0.0, recon=(18, 12, 12))
+    lat.load_gauge(U)
+    fb = lat.to_device(b.cuda(), F64)
+    fx = lat.new_field(F64)
+    st = lat.solve(fx, fb, dirac.CG_NORMAL, tol=1e-10, max_iter=2000, delta=delta, prec_sloppy=sloppy)
+    x = lat.to_natural(fx, F64, device="cpu").numpy()
+    Un = U.numpy()
+    N = lambda v: wilson.apply_M(Un, None, 0.12, wilson.apply_M(Un, None, 0.12, v), dagger=True)
+    assert _oracle_resid(N, x, b.numpy()) <= 1e-10
+    assert abs(st["true_rel_resid"] - _oracle_resid(N, x, b.numpy())) < 1e-12
+    xo, _ = osolv.cg(N, b.numpy(), 1e-12, 2000)
+    assert np.linalg.norm(x - xo) / np.linalg.norm(xo) < 1e-8
+
+
+def _wc_problem(dirac, dims, kappa, block=(4, 4, 4, 4), steps=6, seed=2001):
+    U = synth.wilson_gauge(dims, 0.5, 3, seed)
+    b = synth.wilson_spinor(dims, seed + 1)
+    lat = dirac.Lattice(dims, dirac.WILSON_CLOVER, kappa=kappa, csw=1.0, block=block,
+                        mr_steps=steps, recon=(18, 12, 12))
+    lat.load_gauge(U)
+    Un = U.numpy()
+    A = wilson.clover(Un, 1.0)
+    M = lambda v: wilson.apply_M(Un, A, kappa, v)
+    return lat, b, M
+
+
+@pytest.mark.parametrize("alg,sloppy,precond,delta", [
+    ("BICGSTAB", F64, F64, 0.0), ("BICGSTAB", F32, F32, 0.1), ("BICGSTAB", F16, F16, 0.1),
+    ("GCR", F64, F64, 0.0),
+    ("GCR_DD", F64, F64, 0.0), ("GCR_DD", F32, F16, 1e-3), ("GCR_DD", F16, F16, 0.1),
+])
+def test_wilson_clover_solvers(dirac, alg, sloppy, precond, delta):
+    dims = (8, 8, 8, 8)
+    lat, b, M = _wc_problem(dirac, dims, 0.124)
+    fb = lat.to_device(b.cuda(), F64)
+    fx = lat.new_field(F64)
+    st = lat.solve(fx, fb, getattr(dirac, alg), tol=1e-10, max_iter=4000, k_max=16, delta=delta,
+                   prec_sloppy=sloppy, prec_precond=precond)
+    x = lat.to_natural(fx, F64, device="cpu").numpy()
+    res = _oracle_resid(M, x, b.numpy())
+    assert res <= 1e-10, (alg, st)
+    assert abs(st["true_rel_resid"] - res) < 1e-12
+
+
+def test_gcr_dd_first_cycle_matches_oracle(dirac):
+    """FP64 GCR-DD: after one restart cycle the GPU iterate equals the oracle's
+    Algorithm 1 with the oracle's Schwarz preconditioner (same k_max, same steps)."""
+    dims = (8, 4, 4, 8)
+    lat, b, M = _wc_problem(dirac, dims, 0.124, block=(4, 4, 4, 4), steps=4, seed=77)
+    fb = lat.to_device(b.cuda(), F64)
+    fx = lat.new_field(F64)
+    st = lat.solve(fx, fb, dirac.GCR_DD, tol=1e-10, max_iter=5, k_max=5, delta=0.0,
+                   prec_sloppy=F64, prec_precond=F64, raise_on_error=False)
+    assert st["iters"] == 5 and st["restarts"] == 1
+    x = lat.to_natural(fx, F64, device="cpu").numpy()
+    U = synth.wilson_gauge(dims, 0.5, 3, 77).numpy()
+    A = wilson.clover(U, 1.0)
+    K = lambda r: osolv.schwarz_mr(U, A, 0.124, r, (4, 4, 4, 4), 4)
+    xo, info = osolv.gcr(M, K, b.numpy(), 1e-10, 5, 5, 0.0)
+    assert np.linalg.norm(x - xo) / np.linalg.norm(xo) < 1e-11
+
+
+@pytest.mark.parametrize("sloppy,delta", [(F64, 0.0), (F32, 0.1), (F16, 0.1)])
+def test_staggered_even_cg(dirac, sloppy, delta):
+    dims = (8, 8, 8, 8)
+    m = 0.05
+    fat, lng = synth.asqtad_links(dims, 3001, 3002)
+    b = synth.staggered_spinor(dims, 3003, parity=0)
+    lat = dirac.Lattice(dims, dirac.ASQTAD, mass=m, recon=(18, 12, 12))
+    lat.load_gauge(fat, 1)
+    lat.load_gauge(lng, 2)
+    fb = lat.to_device(b.cuda(), F64, 0)
+    fx = lat.new_field(F64, 0)
+    st = lat.solve(fx, fb, dirac.CG_EVEN_NORMAL, tol=1e-10, max_iter=5000, delta=delta,
+                   prec_sloppy=sloppy)
+    x = lat.to_natural(fx, F64, 0, device="cpu").numpy()
+    fn, ln = fat.numpy(), lng.numpy()
+    even = staggered.parity_mask(dims, 0)[..., None]
+    N = lambda v: staggered.apply_normal(fn, ln, m, v * even) * even
+    assert _oracle_resid(N, x * even, b.numpy()) <= 1e-10, st
+
+
+def test_zero_source_gives_zero(dirac):
+    dims = (4, 4, 4, 4)
+    lat = dirac.Lattice(dims, dirac.WILSON_CLOVER, kappa=0.12, csw=1.0, recon=(18, 12, 12))
+    lat.load_gauge(synth.wilson_gauge(dims, 0.5, 1, 1))
+    fb = lat.new_field(F64)
+    fx = lat.new_field(F64)
+    fx.fill_(3)
+    st = lat.solve(fx, fb, dirac.BICGSTAB, tol=1e-10)
+    assert lat.norm2(fx, F64) == 0.0 and st["iters"] == 0
+
+
+def test_not_converged_status(dirac):
+    dims = (8, 8, 8, 8)
+    lat, b, M = _wc_problem(dirac, dims, 0.124)
+    fb = lat.to_device(b.cuda(), F64)
+    fx = lat.new_field(F64)
+    st = lat.solve(fx, fb, dirac.BICGSTAB, tol=1e-10, max_iter=3, raise_on_error=False)
+    assert st["status"] == "ERR_NOT_CONVERGED" and st["iters"] == 3
+    assert 0 < st["true_rel_resid"] < 1
