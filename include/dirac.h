@@ -74,7 +74,7 @@ typedef struct {
   double kappa;         /* Wilson-clover hopping parameter, kappa = 1/(2(4+m)) (Eq. 2) */
   double csw;           /* clover coefficient; 0 = plain Wilson */
   double mass;          /* asqtad mass m (Eq. 3) */
-  int block[4];         /* Schwarz block extents; each divides dims; block volume <= 512 */
+  int block[4];         /* Schwarz block extents; each divides dims; block volume <= 256 */
   int mr_steps;         /* minimal-residual steps per block solve (Sec. 8.1) */
   int recon[3];         /* dirac_recon per precision F64/F32/F16 for the Wilson links and
                            the asqtad long links (fat links are always 18: not unitary) */

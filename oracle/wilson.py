@@ -156,3 +156,19 @@ def apply_M(U, A, kappa, psi, antiperiodic_t=True, sites=None, dagger=False, blo
 
 def apply_gamma5(psi):
     return np.einsum("st,...tc->...sc", GAMMA5, psi)
+
+
+def apply_M_sites(U, csw, kappa, psi, sites, antiperiodic_t=True, dagger=False, Ahat_codec=None):
+    """M_kappa psi at the listed (N, 4) sites only, with the clover computed at those
+    sites (for sampled checks on lattices too large for a whole-lattice clover array).
+    ``Ahat_codec`` optionally maps Ahat = 1 + 2 kappa A to its stored-precision value."""
+    xs = np.asarray(sites)
+    A = clover(U, csw, xs) if csw else np.zeros((len(xs), 12, 12), dtype=np.complex128)
+    Ahat = np.eye(12) + 2.0 * kappa * A
+    if Ahat_codec is not None:
+        Ahat = Ahat_codec(Ahat)
+    if dagger:
+        Ahat = _dag(Ahat)
+    v = at(psi, xs).reshape(len(xs), 12)
+    out = np.einsum("nij,nj->ni", Ahat, v).reshape(len(xs), 4, 3)
+    return out - kappa * dslash(U, psi, antiperiodic_t, xs, dagger=dagger)

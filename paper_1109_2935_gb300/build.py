@@ -40,13 +40,18 @@ def _headers():
     return hs
 
 
+def _env_flags():
+    """Extra nvcc flags from DIRAC_NVCC_EXTRA (e.g. launch-shape macros when tuning)."""
+    return os.environ.get("DIRAC_NVCC_EXTRA", "").split()
+
+
 def _compile(src, force, extra):
     obj = os.path.join(OUT_DIR, src[:-3] + ".o")
     path = os.path.join(CSRC, src)
     newest = max(os.path.getmtime(p) for p in [path] + _headers())
     if not force and os.path.exists(obj) and os.path.getmtime(obj) >= newest:
         return obj, None
-    cmd = [nvcc(), "-c", path, "-o", obj] + ARCH + FLAGS + extra
+    cmd = [nvcc(), "-c", path, "-o", obj] + ARCH + FLAGS + _env_flags() + extra
     p = subprocess.run(cmd, capture_output=True, text=True)
     if p.returncode != 0:
         return obj, f"{' '.join(cmd)}\n{p.stdout}\n{p.stderr}"

@@ -267,7 +267,7 @@ template <int NR, typename T> struct OpMultiCaxpy {
 
 // ---------------------------------------------------------------- kernels
 template <class Op>
-__global__ void __launch_bounds__(kThreads) map_kernel(Op op, int n) {
+__global__ void __launch_bounds__(kThreads) blas_map_kernel(Op op, int n) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) op(i, nullptr);
 }
 
@@ -297,7 +297,7 @@ __device__ __forceinline__ void block_sum3(double acc[3], double (*sh)[3]) {
 }
 
 template <class Op>
-__global__ void __launch_bounds__(kThreads) reduce_kernel(Op op, int n, double* partials,
+__global__ void __launch_bounds__(kThreads) blas_reduce_kernel(Op op, int n, double* partials,
                                                           unsigned* ticket, double* res) {
   __shared__ double sh[kThreads / 32][3];
   __shared__ bool last;
@@ -346,7 +346,7 @@ static int run_map(Blas* b, const Op& op, int n, cudaStream_t st) {
   int grid = (n + kThreads - 1) / kThreads;
   if (grid > 152 * 16) grid = 152 * 16;
   if (grid < 1) grid = 1;
-  map_kernel<Op><<<grid, kThreads, 0, st>>>(op, n);
+  blas_map_kernel<Op><<<grid, kThreads, 0, st>>>(op, n);
   return check(b, "blas map kernel");
 }
 
@@ -355,7 +355,7 @@ static int run_reduce(Blas* b, const Op& op, int n, double* out, int nout, cudaS
   int grid = (n + kThreads - 1) / kThreads;
   if (grid > kRedBlocks) grid = kRedBlocks;
   if (grid < 1) grid = 1;
-  reduce_kernel<Op><<<grid, kThreads, 0, st>>>(op, n, b->partials, b->ticket, b->dev_res);
+  blas_reduce_kernel<Op><<<grid, kThreads, 0, st>>>(op, n, b->partials, b->ticket, b->dev_res);
   int rc = check(b, "blas reduce kernel");
   if (rc) return rc;
   cudaError_t e = cudaStreamSynchronize(st);

@@ -116,17 +116,42 @@ __device__ __forceinline__ void apply_clover_site(const char* b, int Vh, int cb,
   }
 }
 
+// Launch shape per storage precision (threads per CTA, minimum resident CTAs per SM,
+// which caps registers). FP32/FP16 are memory-latency bound and want many warps in
+// flight; FP64 is FP64-ALU bound on this part.
+#ifndef WILSON_INTERLEAVE
+#define WILSON_INTERLEAVE 32
+#endif
+// Measured on GB300 at 24^3x128 (clover M): FP32 64x8 (128-register cap) 0.199 ms vs
+// 128x1 (up to 255 registers) 0.288 ms; FP16 ~0.178 ms for every shape tried.
+template <int PREC> struct WilsonShape { static constexpr int threads = 64, minb = 10; };
+template <> struct WilsonShape<P32> { static constexpr int threads = 64, minb = 8; };
+template <> struct WilsonShape<P64> { static constexpr int threads = 128, minb = 1; };
+
 template <int PREC, int R, bool FULLM>
-__global__ void __launch_bounds__(128) wilson_kernel(const WilsonArg a) {
+__global__ void __launch_bounds__(WilsonShape<PREC>::threads, WilsonShape<PREC>::minb)
+    wilson_kernel(const WilsonArg a) {
   using T = typename Real<PREC>::T;
   const Geom& g = a.g;
   const int Vh = g.Vh;
   int idx = blockIdx.x * blockDim.x + threadIdx.x;
   int par, cb;
   if (FULLM) {
+    // The two parities alternate every WILSON_INTERLEAVE threads (a warp: the parity
+    // stays warp-uniform): the forward link U_mu(x) read by site x is read again as a
+    // backward link by the neighbour x + mu of the other parity close in time, so it
+    // comes from cache instead of a second DRAM pass over all links.
     if (idx >= 2 * Vh) return;
-    par = idx >= Vh;
-    cb = idx - par * Vh;
+    constexpr int IL = WILSON_INTERLEAVE;
+    const int grp = idx / (2 * IL), k = idx - grp * 2 * IL;
+    if ((grp + 1) * IL <= Vh) {
+      par = k >= IL;
+      cb = grp * IL + k - par * IL;
+    } else {  // last, incomplete pair of groups (Vh not a multiple of IL)
+      const int half = Vh - grp * IL;
+      par = k >= half;
+      cb = grp * IL + k - par * half;
+    }
   } else {
     if (idx >= Vh) return;
     par = a.out_parity;
@@ -134,7 +159,11 @@ __global__ void __launch_bounds__(128) wilson_kernel(const WilsonArg a) {
   }
   int x[4];
   cb_coords(g, cb, par, x);
-  const char* src = a.in[1 - par];
+  // selects, not a runtime index into the parameter arrays (which would copy them
+  // to local memory)
+  const char* src = par ? a.in[0] : a.in[1];
+  const char* self_in = par ? a.in[1] : a.in[0];
+  char* dst = par ? a.out[1] : a.out[0];
   const T sf = a.dagger ? (T)1 : (T)-1;  // forward projector 1 - gamma (adjoint: 1 + gamma)
   const T sb = -sf;
 
@@ -186,7 +215,7 @@ __global__ void __launch_bounds__(128) wilson_kernel(const WilsonArg a) {
   T out[24];
   if (FULLM) {
     T self[24];
-    SpinorIO<PREC, 24>::load(a.in[par], Vh, cb, self);
+    SpinorIO<PREC, 24>::load(self_in, Vh, cb, self);
     C<T> sv[12], av[12];
 #pragma unroll
     for (int k = 0; k < 12; ++k) sv[k] = C<T>{self[2 * k], self[2 * k + 1]};
@@ -213,13 +242,14 @@ __global__ void __launch_bounds__(128) wilson_kernel(const WilsonArg a) {
         out[6 * s + 2 * c + 1] = acc[s][c].i;
       }
   }
-  SpinorIO<PREC, 24>::store(a.out[par], Vh, cb, out);
+  SpinorIO<PREC, 24>::store(dst, Vh, cb, out);
 }
 
 template <int PREC>
 void launch_wilson_prec(int recon, bool fullm, const WilsonArg& a, cudaStream_t st) {
   int n = fullm ? 2 * a.g.Vh : a.g.Vh;
-  dim3 block(128), grid((n + 127) / 128);
+  constexpr int T = WilsonShape<PREC>::threads;
+  dim3 block(T), grid((n + T - 1) / T);
   if (recon == 18) {
     if (fullm) wilson_kernel<PREC, 18, true><<<grid, block, 0, st>>>(a);
     else wilson_kernel<PREC, 18, false><<<grid, block, 0, st>>>(a);

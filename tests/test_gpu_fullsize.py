@@ -1,0 +1,101 @@
+"""Parity at the full workload sizes, in the launch configurations the benchmark
+times: the 24^3x128 Wilson-clover operator (FP64-18, FP32-12, FP16-12; full M, M^dagger
+and the parity dslash) and the 48^3x144 asqtad parity dslash. The oracle evaluates the
+operators one site at a time at a random sample of output sites."""
+import numpy as np
+import pytest
+import torch
+
+from helpers import F16, F32, F64, check, dec_clover_hat, dec_spinor
+from oracle import staggered, wilson
+from oracle.lattice import all_coords
+from paper_1109_2935_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _sample(dims, n, parity=None, seed=0):
+    c = all_coords(dims)
+    if parity is not None:
+        c = c[c.sum(1) % 2 == parity]
+    rng = np.random.default_rng(seed)
+    s = c[rng.choice(len(c), n, replace=False)]
+    # always include the lattice corners (wrapping hops in every direction)
+    corners = np.array([[0, 0, 0, 0], [dims[0] - 1, dims[1] - 1, dims[2] - 1, dims[3] - 1]])
+    if parity is not None:
+        corners = corners[corners.sum(1) % 2 == parity]
+    return np.concatenate([s, corners])
+
+
+def _at(nat, s):
+    return nat[s[:, 3], s[:, 2], s[:, 1], s[:, 0]]
+
+
+@pytest.fixture(scope="module")
+def wilson_full(dirac):
+    dims = (24, 24, 24, 128)
+    kappa, csw = 0.1350, 1.0
+    U = synth.wilson_gauge(dims, 0.5, 3, 2001, device="cuda")
+    psi = synth.wilson_spinor(dims, 2002, device="cuda")
+    lat = dirac.Lattice(dims, dirac.WILSON_CLOVER, kappa=kappa, csw=csw, block=(4, 4, 4, 4),
+                        mr_steps=6, recon=(18, 12, 12))
+    lat.load_gauge(U)
+    yield lat, U.cpu().numpy(), psi, kappa, csw
+    lat.close()
+
+
+@pytest.mark.parametrize("prec", [F64, F32, F16])
+@pytest.mark.parametrize("dagger", [False, True])
+def test_wilson_clover_24x128(dirac, wilson_full, prec, dagger):
+    lat, Un, psi, kappa, csw = wilson_full
+    dims = lat.dims
+    x = lat.to_device(psi, prec)
+    y = lat.new_field(prec)
+    (lat.apply_dagger if dagger else lat.apply)(y, x, dirac.PARITY_FULL, prec)
+    got = lat.to_natural(y, prec, device="cpu").numpy()
+    s = _sample(dims, 384, seed=prec + 10 * dagger)
+    psi_d = dec_spinor(psi.cpu().numpy(), prec)
+    # F32/F16 links: the oracle takes the FP64 links; the kernel's link rounding is
+    # within the FP32 bound, and within the FP16 per-site bound
+    ref = wilson.apply_M_sites(Un, csw, kappa, psi_d, s, True, dagger,
+                               Ahat_codec=lambda A: dec_clover_hat(A, prec))
+    check(_at(got, s), ref, prec, 24, f"24^3x128 M prec={prec} dag={dagger}")
+
+
+@pytest.mark.parametrize("parity", [0, 1])
+def test_wilson_dslash_24x128_f32(dirac, wilson_full, parity):
+    lat, Un, psi, kappa, csw = wilson_full
+    dims = lat.dims
+    src = lat.to_device(psi, F32, 1 - parity)
+    out = lat.new_field(F32, parity)
+    lat.apply(out, src, parity, F32)
+    got = lat.to_natural(out, F32, parity, device="cpu").numpy()
+    s = _sample(dims, 384, parity, seed=3 + parity)
+    m = ((np.indices(psi.shape[:4]).sum(0)) % 2 == 1 - parity)
+    psi_d = dec_spinor(psi.cpu().numpy(), F32) * m[..., None, None]
+    ref = wilson.dslash(Un, psi_d, True, s)
+    check(_at(got, s), ref, F32, 24, f"24^3x128 D_{parity}")
+
+
+def test_asqtad_48x144(dirac):
+    dims = (48, 48, 48, 144)
+    fat, lng = synth.asqtad_links(dims, 3001, 3002, device="cuda")
+    psi = synth.staggered_spinor(dims, 3003, device="cuda")
+    lat = dirac.Lattice(dims, dirac.ASQTAD, mass=0.01, recon=(18, 12, 12))
+    lat.load_gauge(fat, 1)
+    lat.load_gauge(lng, 2)
+    fat_n, lng_n, psi_n = fat.cpu().numpy(), lng.cpu().numpy(), psi.cpu().numpy()
+    del fat, lng
+    torch.cuda.empty_cache()
+    for prec in (F64, F32, F16):
+        for parity in (0, 1):
+            src = lat.to_device(psi, prec, 1 - parity)
+            out = lat.new_field(prec, parity)
+            lat.apply(out, src, parity, prec)
+            got = lat.to_natural(out, prec, parity, device="cpu").numpy()
+            s = _sample(dims, 256, parity, seed=7 * prec + parity)
+            m = ((np.indices(psi_n.shape[:4]).sum(0)) % 2 == 1 - parity)
+            ref = staggered.dslash(fat_n, lng_n, dec_spinor(psi_n, prec) * m[..., None], True, s)
+            check(_at(got, s), ref, prec, 6, f"48^3x144 asqtad D_{parity} prec={prec}")
+            del src, out
+    lat.close()
