@@ -143,6 +143,30 @@ int dirac_caxpy_norm(dirac_ctx* ctx, double a_re, double a_im, const void* x, vo
 int dirac_convert(dirac_ctx* ctx, void* dst, dirac_prec dprec, const void* src, dirac_prec sprec,
                   dirac_parity parity, void* stream);
 
+/* Allocation-free inner product, for callers that must not allocate GPU memory.
+ * (The paper has no counterpart; this is a library-usage addition.)
+ * Who needs it: a host application that has already handed all of the GPU's memory
+ * to its own pool allocator, or that calls in from a stream-ordered section where a
+ * cudaMalloc would implicitly synchronise the device and stall its other streams,
+ * cannot create a dirac_ctx (dirac_create allocates its reduction scratch). This
+ * entry point needs no context and allocates nothing: it computes
+ *     result[0] + i result[1] = (x, y) = sum conj(x_i) y_i,   result[2] = ||x||^2
+ * for two spinor fields in the device layout (reals_per_site 24 Wilson or 6
+ * staggered; sites_per_parity = Vh; parity FULL for a full field), accumulating in
+ * FP64 like dirac_cdot, and writes the three doubles to the caller's DEVICE pointer
+ * `result` without synchronising the stream.
+ * Scratch: a fixed 98,312-byte device array inside the library (every GPU that loads
+ * the library holds it until the process exits). One call covers at most 8,388,608
+ * sites (npar * sites_per_parity); larger fields are rejected with DIRAC_ERR_ARG and
+ * a message in `err` (err may be NULL; err_len bytes including the terminator).
+ * Every call shares the array: calls that overlap on the GPU (other streams or other
+ * host threads) race and give wrong results; serialise them. The first call on each
+ * device looks up the array's device address (once per device, with that device
+ * current); make that first call before any stream capture. */
+int dirac_cdot_noalloc(const void* x, const void* y, dirac_prec prec, int reals_per_site,
+                       long long sites_per_parity, dirac_parity parity, double* result,
+                       void* stream, char* err, size_t err_len);
+
 typedef enum {
   DIRAC_SOLVER_CG_NORMAL = 0,      /* CG on M^dagger M x = b, full lattice (Sec. 3.1) */
   DIRAC_SOLVER_CG_EVEN_NORMAL = 1, /* CG on (M^dagger M)_ee x_e = b_e, asqtad (Sec. 3.1) */

@@ -8,6 +8,7 @@
 // each block writes a partial sum, the last block to finish adds the partials in a
 // fixed order and writes the result into mapped pinned host memory.
 #include <cstring>
+#include <mutex>
 #include <string>
 
 #include "internal.h"
@@ -451,3 +452,103 @@ int blas_multi_caxpy(Blas* b, int n, const double* cr, const double* ci, const F
 }
 
 }  // namespace dirac
+
+// ======================================================================== no-alloc
+// dirac_cdot_noalloc: the reduction above, for callers that must not allocate GPU
+// memory. Its scratch (per-block partial sums and the last-block ticket) is the
+// file-scope array below, which every GPU that loads the library holds until exit.
+namespace dirac {
+
+static constexpr int kNoAllocThreads = 256;
+static constexpr int kNoAllocSitesPerThread = 8;
+static constexpr int kNoAllocMaxBlocks = 4096;
+// sites one call may cover: 4096 blocks x 256 threads x 8 sites = 8,388,608
+static constexpr long long kNoAllocMaxSites =
+    (long long)kNoAllocMaxBlocks * kNoAllocThreads * kNoAllocSitesPerThread;
+// 3 partial sums per block, then one 64-bit slot for the ticket: 98,312 bytes
+static __device__ __align__(256) unsigned long long g_noalloc_scratch[3 * kNoAllocMaxBlocks + 1];
+
+static std::mutex g_noalloc_mu;
+static void* g_noalloc_addr[128] = {};  // device address of the array, per device
+
+static int noalloc_fail(char* err, size_t len, int code, const std::string& msg) {
+  if (err && len) {
+    size_t n = msg.size() < len - 1 ? msg.size() : len - 1;
+    std::memcpy(err, msg.data(), n);
+    err[n] = 0;
+  }
+  return code;
+}
+
+}  // namespace dirac
+
+extern "C" int dirac_cdot_noalloc(const void* x, const void* y, dirac_prec prec, int reals_per_site,
+                                  long long sites_per_parity, dirac_parity parity, double* result,
+                                  void* stream, char* err, size_t err_len) {
+  using namespace dirac;
+  if (err && err_len) err[0] = 0;
+  if (!x || !y || !result)
+    return noalloc_fail(err, err_len, DIRAC_ERR_ARG, "dirac_cdot_noalloc: null pointer");
+  if (prec != DIRAC_PREC_F64 && prec != DIRAC_PREC_F32 && prec != DIRAC_PREC_F16)
+    return noalloc_fail(err, err_len, DIRAC_ERR_ARG, "dirac_cdot_noalloc: unknown precision");
+  if (reals_per_site != 24 && reals_per_site != 6)
+    return noalloc_fail(err, err_len, DIRAC_ERR_ARG, "dirac_cdot_noalloc: reals_per_site must be 24 or 6");
+  if (parity < DIRAC_PARITY_FULL || parity > DIRAC_PARITY_ODD || sites_per_parity < 1 ||
+      sites_per_parity > 0x3fffffffLL)
+    return noalloc_fail(err, err_len, DIRAC_ERR_ARG, "dirac_cdot_noalloc: bad parity or size");
+  const long long n = (parity == DIRAC_PARITY_FULL ? 2 : 1) * sites_per_parity;
+  if (n > kNoAllocMaxSites)
+    return noalloc_fail(err, err_len, DIRAC_ERR_ARG,
+                        "dirac_cdot_noalloc: " + std::to_string(n) + " sites exceed the maximum of " +
+                            std::to_string(kNoAllocMaxSites) + " for its fixed scratch array");
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 128)
+    return noalloc_fail(err, err_len, DIRAC_ERR_CUDA, "dirac_cdot_noalloc: cudaGetDevice failed");
+  void* base = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+      // once per device, with that device current: the host-side name of the array is
+      // not a device address, so ask the runtime for the real one
+      cudaError_t e = cudaGetSymbolAddress(&g_noalloc_addr[dev], g_noalloc_scratch);
+      if (e != cudaSuccess) {
+        g_noalloc_addr[dev] = nullptr;
+        return noalloc_fail(err, err_len, DIRAC_ERR_CUDA,
+                            std::string("dirac_cdot_noalloc: cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+      }
+    }
+    base = g_noalloc_addr[dev];
+  }
+  double* partials = reinterpret_cast<double*>(base);
+  unsigned* ticket = reinterpret_cast<unsigned*>(reinterpret_cast<unsigned long long*>(base) + 3 * kNoAllocMaxBlocks);
+  cudaStream_t st = (cudaStream_t)stream;
+  // the ticket must start at zero; the partial sums are written before they are read
+  if (cudaMemsetAsync(ticket, 0, sizeof(unsigned long long), st) != cudaSuccess)
+    return noalloc_fail(err, err_len, DIRAC_ERR_CUDA, "dirac_cdot_noalloc: clearing the ticket failed");
+  FieldRef fx, fy;
+  fx.p = (char*)x;
+  fy.p = (char*)y;
+  fx.prec = fy.prec = prec;
+  fx.nr = fy.nr = reals_per_site;
+  fx.Vh = fy.Vh = (int)sites_per_parity;
+  fx.npar = fy.npar = parity == DIRAC_PARITY_FULL ? 2 : 1;
+  fx.hb = fy.hb = spinor_half_bytes(prec, reals_per_site, sites_per_parity);
+  const long long per_block = (long long)kNoAllocThreads * kNoAllocSitesPerThread;
+  const int grid = (int)((n + per_block - 1) / per_block);
+  const bool dbl = prec == DIRAC_PREC_F64;
+  if (reals_per_site == 24) {
+    if (dbl) blas_reduce_kernel<OpCdotNorm<24, double>><<<grid, kNoAllocThreads, 0, st>>>(
+        OpCdotNorm<24, double>{fx, fy}, (int)n, partials, ticket, result);
+    else blas_reduce_kernel<OpCdotNorm<24, float>><<<grid, kNoAllocThreads, 0, st>>>(
+        OpCdotNorm<24, float>{fx, fy}, (int)n, partials, ticket, result);
+  } else {
+    if (dbl) blas_reduce_kernel<OpCdotNorm<6, double>><<<grid, kNoAllocThreads, 0, st>>>(
+        OpCdotNorm<6, double>{fx, fy}, (int)n, partials, ticket, result);
+    else blas_reduce_kernel<OpCdotNorm<6, float>><<<grid, kNoAllocThreads, 0, st>>>(
+        OpCdotNorm<6, float>{fx, fy}, (int)n, partials, ticket, result);
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess)
+    return noalloc_fail(err, err_len, DIRAC_ERR_CUDA, std::string("dirac_cdot_noalloc: launch: ") + cudaGetErrorString(e));
+  return DIRAC_OK;
+}

@@ -74,6 +74,8 @@ _SIGS = {
     "dirac_caxpy_norm": (_ci, [_vp, _cd, _cd, _vp, _vp, _ci, _ci, _pd, _vp]),
     "dirac_convert": (_ci, [_vp, _vp, _ci, _vp, _ci, _ci, _vp]),
     "solve": (_ci, [_vp, _vp, _vp, ctypes.POINTER(SolverParams), ctypes.POINTER(SolverStats), _vp]),
+    "dirac_cdot_noalloc": (_ci, [_vp, _vp, _ci, _ci, ctypes.c_longlong, _ci, _vp, _vp,
+                                 ctypes.c_char_p, _sz]),
 }
 EXPORTED = tuple(_SIGS)
 for _name, (_res, _args) in _SIGS.items():
