@@ -210,6 +210,9 @@ def main():
     ap.add_argument("--no-solve", action="store_true", help="skip the solve section")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer e2e timing")
+    ap.add_argument("--no-asqtad", action="store_true", help="skip the asqtad rows")
+    ap.add_argument("--asqtad-dims", type=int, nargs=4, default=[48, 48, 48, 144],
+                    help="asqtad lattice (48^3x144 unless profiling a smaller case)")
     ap.add_argument("--dims", type=int, nargs=4, default=list(DIMS),
                     help="lattice extents (profiling cases use a smaller lattice)")
     ap.add_argument("--precs", default="f64,f32,f16", help="precisions to keep and time")
@@ -287,6 +290,9 @@ def main():
                           "frac_of_hbm": round(gbs / peak, 4),
                           "gflops": round(SITE_FLOPS * V / (ms / 1e3) / 1e9, 1)}
 
+    # the other rows of the path on the same lattice: parity dslash, Schwarz K, BLAS
+    rows = measure_wilson_rows(lat, dirac, fields, precs, stream, peak)
+
     # e2e: through the C ABI with host (pinned) natural-layout buffers
     e2e = None
     if not args.no_e2e:
@@ -307,8 +313,117 @@ def main():
                "sample": f"FP64 numpy oracle, M at {orc.n} fixed random sites of 24^3x128, "
                          f"3 applications ({sum(ts):.2f} s), FP64 1536 B/site count"}
     workload = "wilson-clover %dx%dx%dx%d csw=1.0 kappa=0.135 sigma=0.5 smear=3" % dims
+    del fields
+    lat.close()
+    torch.cuda.empty_cache()
+    if not args.no_asqtad:
+        ad = tuple(args.asqtad_dims)
+        rows["asqtad_%dx%dx%dx%d" % ad] = measure_asqtad(dirac, synth, dev, stream, peak,
+                                                         not args.no_solve, ad)
     return finish(args, world, rank, dev, value, total_ms_max, achieved, peak, peak_kind,
-                  bytes_per_launch, per_prec, clk, e2e, cpu, solves, wall, workload, V)
+                  bytes_per_launch, per_prec, clk, e2e, cpu, solves, wall, workload, V, rows)
+
+
+# FP32 peak for ALU-bound kernels: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+# parity dslash, algorithmic bytes per OUTPUT site: 8 links + spinor in + spinor out
+HOP_BYTES = {"f64": 8 * 18 * 8 + 2 * 24 * 8, "f32": 8 * 12 * 4 + 2 * 24 * 4,
+             "f16": 8 * 12 * 2 + 2 * 52}
+# asqtad parity dslash per OUTPUT site: 8 fat (18 reals) + 8 long (18 / 12 / 12) + in + out
+STAG_BYTES = {"f64": 8 * 18 * 8 + 8 * 18 * 8 + 2 * 6 * 8, "f32": 8 * 18 * 4 + 8 * 12 * 4 + 2 * 6 * 4,
+              "f16": 8 * 18 * 2 + 8 * 12 * 2 + 2 * 16}
+
+
+def _event_time(fn, n, stream, warm=3):
+    import torch
+    for _ in range(warm):
+        fn()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(n):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / n
+
+
+def measure_wilson_rows(lat, dirac, fields, precs, stream, peak):
+    import time as _t
+    V, Vh = lat.volume, lat.volume // 2
+    out = {"dslash_parity": {}, "schwarz": {}, "blas_caxpy_norm": {}}
+    for name in precs:
+        pid = PREC_ID[name]
+        x, y = fields[name]
+        hb = lat.field_bytes(pid, 0)
+        n = 20 if name == "f64" else 100
+        ms = _event_time(lambda: lat.apply(y[:hb], x[hb:], 0, pid, stream), n, stream)
+        gbs = HOP_BYTES[name] * Vh / (ms / 1e3) / 1e9
+        out["dslash_parity"][name] = {"ms": round(ms, 5), "alg_GBps": round(gbs, 1),
+                                      "frac_of_hbm": round(gbs / peak, 4)}
+        n = 3 if name == "f64" else 20
+        ms = _event_time(lambda: lat.schwarz(y, x, pid, stream), n, stream, warm=1)
+        flops = MR_STEPS * (SITE_FLOPS + 192) * V
+        tf = flops / (ms / 1e3) / 1e12
+        out["schwarz"][name] = {"ms": round(ms, 4), "tflops": round(tf, 2),
+                                "frac_of_fp32_peak": round(tf / FP32_PEAK_TFLOPS, 4),
+                                "bound": "alu", "flops_per_site": MR_STEPS * (SITE_FLOPS + 192)}
+        # BLAS: y += a x with ||y||^2 through the C ABI (includes its stream sync)
+        reps = 20
+        t0 = _t.perf_counter()
+        for _ in range(reps):
+            lat.caxpy_norm(1e-3, x, y, pid, stream=stream)
+        ms = (_t.perf_counter() - t0) / reps * 1e3
+        fb = lat.field_bytes(pid)
+        out["blas_caxpy_norm"][name] = {"ms_per_call_incl_sync": round(ms, 4),
+                                        "GBps_incl_sync": round(3 * fb / (ms / 1e3) / 1e9, 1)}
+    out["schwarz"]["fp32_peak_tflops"] = round(FP32_PEAK_TFLOPS, 1)
+    return out
+
+
+def measure_asqtad(dirac, synth, dev, stream, peak, do_solve, dims):
+    """Asqtad parity dslash and even-site normal operator (48^3x144, m = 0.01), and
+    CG on (M^dagger M)_ee, mixed FP64/FP32 vs plain FP64. (An FP16 Krylov space
+    stagnates near 3e-4 on this operator, so it is not part of the comparison.)"""
+    import torch
+    fat, lng = synth.asqtad_links(dims, 3001, 3002, device=dev)
+    src = synth.staggered_spinor(dims, 3003, device=dev, parity=0)
+    lat = dirac.Lattice(dims, dirac.ASQTAD, mass=0.01, recon=(18, 12, 12))
+    lat.load_gauge(fat, 1)
+    lat.load_gauge(lng, 2)
+    del fat, lng
+    torch.cuda.empty_cache()
+    Vh = lat.volume // 2
+    res = {"dslash_parity": {}, "normal_even": {}}
+    for name, pid in PREC_ID.items():
+        xin = lat.to_device(src, pid, 0)
+        yout = lat.new_field(pid, 1)
+        n = 10 if name == "f64" else 50
+        ms = _event_time(lambda: lat.apply(yout, xin, 1, pid, stream), n, stream)
+        gbs = STAG_BYTES[name] * Vh / (ms / 1e3) / 1e9
+        res["dslash_parity"][name] = {"ms": round(ms, 4), "alg_GBps": round(gbs, 1),
+                                      "frac_of_hbm": round(gbs / peak, 4),
+                                      "gflops": round(1146 * Vh / (ms / 1e3) / 1e9, 1)}
+        ye = lat.new_field(pid, 0)
+        ms = _event_time(lambda: lat.apply_normal(ye, xin, 0, pid, stream), n // 2, stream)
+        res["normal_even"][name] = {"ms": round(ms, 4),
+                                    "alg_GBps": round(2 * STAG_BYTES[name] * Vh / (ms / 1e3) / 1e9, 1)}
+        del xin, yout, ye
+    if do_solve:
+        b = lat.to_device(src, dirac.F64, 0)
+        x = lat.new_field(dirac.F64, 0)
+        sol = {}
+        for tag, sp, delta in (("cg_mixed_f32", dirac.F32, 0.1), ("cg_f64", dirac.F64, 0.0)):
+            torch.cuda.synchronize()
+            st = lat.solve(x, b, dirac.CG_EVEN_NORMAL, tol=1e-10, max_iter=4000, delta=delta,
+                           prec_sloppy=sp, raise_on_error=False)
+            sol[tag] = {k: (float(f"{v:.4g}") if isinstance(v, float) else v) for k, v in st.items()}
+        for tag in ("cg_mixed_f32",):
+            if sol[tag]["status"] == "OK" and sol["cg_f64"]["status"] == "OK":
+                sol[tag + "_speedup_vs_f64"] = round(sol["cg_f64"]["seconds"] / sol[tag]["seconds"], 3)
+        res["solve_cg_even_m0.01"] = sol
+    lat.close()
+    return res
 
 
 def time_e2e(lat, dirac, src, fields, stream, args, world, dev, bytes_per_launch):
@@ -342,7 +457,7 @@ def time_e2e(lat, dirac, src, fields, stream, args, world, dev, bytes_per_launch
 
 
 def finish(args, world, rank, dev, value, total_ms_max, achieved, peak, peak_kind,
-           bytes_per_launch, per_prec, clk, e2e, cpu, solves, wall, workload, V):
+           bytes_per_launch, per_prec, clk, e2e, cpu, solves, wall, workload, V, rows):
     if rank == 0:
         line = {
             "metric": "Wilson-clover dslash HBM GB/s (algorithmic bytes, % of HBM roofline); "
@@ -366,9 +481,10 @@ def finish(args, world, rank, dev, value, total_ms_max, achieved, peak, peak_kin
             "gpu_launches": args.steps,
             "cpu_baseline": cpu,
             "solve": solves,
+            "rows": rows,
             "wall_s_timed": round(wall, 4),
         }
-        traffic = _traffic_from_profile()
+        traffic = _traffic_from_profile(tuple(args.dims))
         if traffic:
             line["roofline"]["traffic"] = traffic
         print(json.dumps(line))
@@ -378,16 +494,27 @@ def finish(args, world, rank, dev, value, total_ms_max, achieved, peak, peak_kin
     return 0
 
 
-def _traffic_from_profile():
-    """DRAM bytes per launch of the headline kernel from the committed ncu summary,
-    if it records one for the current kernel."""
-    p = os.path.join(ROOT, "profiles", "wilson_clover_M_f32_24x24x24x128.json")
+def _traffic_from_profile(dims):
+    """DRAM bytes per launch of the headline kernel from the committed ncu summary, or
+    None when the summary does not cover this lattice or the kernel sources changed
+    since the counters were taken (the summary records a hash of them)."""
+    import hashlib
+    import re
+    src = os.path.join(ROOT, "paper_1109_2935_gb300", "csrc")
+    h = hashlib.sha256()
+    for f in ("field.cuh", "wilson.cuh"):
+        with open(os.path.join(src, f), "rb") as fh:
+            h.update(fh.read())
     try:
-        with open(p) as f:
-            d = json.load(f)
-        return d.get("dram_bytes_per_launch")
-    except Exception:
+        with open(os.path.join(ROOT, "profiles", "wilson_clover_M_f32_24x24x24x64.md")) as f:
+            text = f.read()
+    except OSError:
         return None
+    m = re.search(r"csrc/wilson.cuh\): ([0-9a-f]{16})", text)
+    t = re.search(r"dram_bytes_per_launch_%dx%dx%dx%d: (\d+)" % dims, text)
+    if not m or not t or m.group(1) != h.hexdigest()[:16]:
+        return None
+    return int(t.group(1))
 
 
 def run_solves(dirac, synth, U, src, dev):
@@ -411,7 +538,7 @@ def run_solves(dirac, synth, U, src, dev):
             torch.cuda.synchronize()
             st = lat.solve(x, b, alg, tol=1e-10, max_iter=budget if alg != dirac.GCR_DD else budget // 4,
                            k_max=16, delta=delta, prec_sloppy=sp, prec_precond=pp, raise_on_error=False)
-            res[name] = {k: (round(v, 6) if isinstance(v, float) else v) for k, v in st.items()}
+            res[name] = {k: (float(f"{v:.4g}") if isinstance(v, float) else v) for k, v in st.items()}
         for alg in ("gcr_dd", "bicgstab"):
             a, b_ = res.get(f"{alg}_mixed"), res.get(f"{alg}_f64")
             if a and b_ and a["status"] == "OK" and b_["status"] == "OK":
