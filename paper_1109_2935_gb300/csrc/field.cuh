@@ -270,27 +270,34 @@ template <int PREC, int R>
 struct LinkIO {
   using T = typename Real<PREC>::T;
   static constexpr int W = PREC == P64 ? 8 : (PREC == P32 ? 4 : 2);
-  // load link (mu, par, cb) from the gauge base pointer
-  __device__ static void load(const char* base, int Vh, int mu, int par, int cb, Link<T>& U) {
-    const char* plane = base + (size_t)(mu * 2 + par) * link_plane_bytes(R, W, Vh);
+  // storage chunks per link: bytes per chunk and chunk count
+  static constexpr int kChunkBytes = PREC == P64 ? 16
+                                   : PREC == P32 ? (R == 18 ? 8 : 16)
+                                   : (R == 18 ? 4 : (R == 12 ? 8 : 16));
+  static constexpr int kChunks = R * W / kChunkBytes;
+
+  // load the link at index i of a plane whose chunk arrays have `stride` entries
+  // (NC: read-only-cache loads from global memory; otherwise plain loads, e.g. smem)
+  template <bool NC = true>
+  __device__ static void load_plane(const char* plane, int stride, int i, Link<T>& U) {
     T v[R];
     if constexpr (PREC == P64) {
 #pragma unroll
       for (int k = 0; k < R / 2; ++k) {
-        double2 q = ldg_chunk<double2>(plane + ((size_t)k * Vh + cb) * 16);
+        double2 q = ld_chunk<double2, NC>(plane + ((size_t)k * stride + i) * 16);
         v[2 * k] = (T)q.x; v[2 * k + 1] = (T)q.y;
       }
     } else if constexpr (PREC == P32) {
       if constexpr (R == 18) {
 #pragma unroll
         for (int k = 0; k < 9; ++k) {
-          float2 q = ldg_chunk<float2>(plane + ((size_t)k * Vh + cb) * 8);
+          float2 q = ld_chunk<float2, NC>(plane + ((size_t)k * stride + i) * 8);
           v[2 * k] = q.x; v[2 * k + 1] = q.y;
         }
       } else {
 #pragma unroll
         for (int k = 0; k < R / 4; ++k) {
-          float4 q = ldg_chunk<float4>(plane + ((size_t)k * Vh + cb) * 16);
+          float4 q = ld_chunk<float4, NC>(plane + ((size_t)k * stride + i) * 16);
           v[4 * k] = q.x; v[4 * k + 1] = q.y; v[4 * k + 2] = q.z; v[4 * k + 3] = q.w;
         }
       }
@@ -298,19 +305,19 @@ struct LinkIO {
       if constexpr (R == 18) {
 #pragma unroll
         for (int k = 0; k < 9; ++k) {
-          float2 f = __half22float2(ldg_chunk<__half2>(plane + ((size_t)k * Vh + cb) * 4));
+          float2 f = __half22float2(ld_chunk<__half2, NC>(plane + ((size_t)k * stride + i) * 4));
           v[2 * k] = f.x; v[2 * k + 1] = f.y;
         }
       } else if constexpr (R == 12) {
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-          uint2 q = ldg_chunk<uint2>(plane + ((size_t)k * Vh + cb) * 8);
+          uint2 q = ld_chunk<uint2, NC>(plane + ((size_t)k * stride + i) * 8);
           const __half2* h = reinterpret_cast<const __half2*>(&q);
           float2 f0 = __half22float2(h[0]), f1 = __half22float2(h[1]);
           v[4 * k] = f0.x; v[4 * k + 1] = f0.y; v[4 * k + 2] = f1.x; v[4 * k + 3] = f1.y;
         }
       } else {
-        int4 q = ldg_chunk<int4>(plane + (size_t)cb * 16);
+        int4 q = ld_chunk<int4, NC>(plane + (size_t)i * 16);
         float f[8];
         unpack_half8(q, f);
 #pragma unroll
@@ -326,6 +333,10 @@ struct LinkIO {
         for (int b = 0; b < 3; ++b) U.m[a][b] = C<T>{v[6 * a + 2 * b], v[6 * a + 2 * b + 1]};
       if constexpr (R == 12) reconstruct12(U);
     }
+  }
+  // load link (mu, par, cb) from the gauge base pointer
+  __device__ static void load(const char* base, int Vh, int mu, int par, int cb, Link<T>& U) {
+    load_plane<true>(base + (size_t)(mu * 2 + par) * link_plane_bytes(R, W, Vh), Vh, cb, U);
   }
   // store the compressed form of a full FP64 link
   __device__ static void store(char* base, int Vh, int mu, int par, int cb, const double u[18]) {
@@ -429,6 +440,34 @@ template <> struct CloverIO<P16> {
     reinterpret_cast<float*>(b + (size_t)144 * Vh)[cb] = m;
   }
 };
+
+// The 36 reals of chirality block `blk` (0 or 1) of site i, from a clover array with
+// chunk stride `stride` (global memory with NC, shared memory without).
+template <int PREC, bool NC, typename T>
+__device__ __forceinline__ void clover_block(const char* b, int stride, int i, int blk, T v[36]) {
+  if constexpr (PREC == P64) {
+#pragma unroll
+    for (int k = 0; k < 18; ++k) {
+      double2 q = ld_chunk<double2, NC>(b + ((size_t)(18 * blk + k) * stride + i) * 16);
+      v[2 * k] = (T)q.x; v[2 * k + 1] = (T)q.y;
+    }
+  } else if constexpr (PREC == P32) {
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      float4 q = ld_chunk<float4, NC>(b + ((size_t)(9 * blk + k) * stride + i) * 16);
+      v[4 * k] = q.x; v[4 * k + 1] = q.y; v[4 * k + 2] = q.z; v[4 * k + 3] = q.w;
+    }
+  } else {
+    // reals 36*blk .. 36*blk+35 live in 8-half chunks 4*blk .. 4*blk+4
+    const float n = ld_chunk<float, NC>(b + (size_t)144 * stride + (size_t)i * 4);
+    float f[40];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) unpack_half8(ld_chunk<int4, NC>(b + ((size_t)(4 * blk + k) * stride + i) * 16), f + 8 * k);
+    const int off = 4 * blk;  // block 1 starts 4 halves into chunk 4
+#pragma unroll
+    for (int k = 0; k < 36; ++k) v[k] = f[k + off] * n;
+  }
+}
 
 // y = A x for one Hermitian 6x6 block stored as above (d[6], then 15 complex L_ij, i>j)
 template <typename T>

@@ -9,11 +9,12 @@
 // wrapped target lies in the same block; a block spanning a whole lattice extent
 // keeps that extent's periodic / antiperiodic wrap.
 //
-// FP32/FP16 storage: the block's residual r, its 4*|B| forward links (decoded to
-// 18 FP32 reals) and its clover blocks are staged in shared memory; x and p live in
-// registers; reductions are warp shuffles plus one shared-memory stage.
-// FP64 storage: r is staged in shared memory, links and clover are read through
-// the read-only cache.
+// FP32/FP16 storage: the block's forward links and clover are copied into shared
+// memory in their storage format (raw chunks: binary16 stays binary16, so an FP16
+// block needs 87 KB and two CTAs fit on an SM) and decoded on use; the residual r
+// lives in shared memory in FP32, x in registers; reductions are warp shuffles plus
+// one shared-memory stage. FP64 storage: r in shared memory, links and clover read
+// through the read-only cache.
 #include "internal.h"
 #include "wilson.cuh"
 
@@ -31,6 +32,17 @@ struct SchwarzArg {
   int nb[4];       // blocks per dimension
   int steps;
   double kappa;
+};
+
+template <int PREC, int R>
+struct SchwarzLayout {
+  using T = typename Real<PREC>::T;
+  static constexpr bool kStage = PREC != P64;
+  static constexpr int kLinkSite = kStage ? 4 * LinkIO<PREC, R>::kChunks * LinkIO<PREC, R>::kChunkBytes : 0;
+  static constexpr int kClovSite = kStage ? (PREC == P32 ? 288 : 148) : 0;
+  static constexpr int kRSite = 24 * (int)sizeof(T);
+  static constexpr int kSite = kRSite + kLinkSite + kClovSite;  // bytes of smem per block site
+  static constexpr int kMinBlocks = PREC == P16 ? 2 : 1;
 };
 
 template <typename T>
@@ -52,16 +64,25 @@ __device__ __forceinline__ void block_sum3(T v[3], T (*sh)[3], int nwarp) {
   }
 }
 
-// Shared-memory layout (floats, FP32 compute): r[24][nbs] | links[4][18][nbs] | clov[72][nbs]
+template <int CB>
+__device__ __forceinline__ void copy_chunk(char* dst, const char* src) {
+  if constexpr (CB == 16) *reinterpret_cast<int4*>(dst) = __ldg(reinterpret_cast<const int4*>(src));
+  else if constexpr (CB == 8) *reinterpret_cast<int2*>(dst) = __ldg(reinterpret_cast<const int2*>(src));
+  else *reinterpret_cast<int*>(dst) = __ldg(reinterpret_cast<const int*>(src));
+}
+
 template <int PREC, int R>
-__global__ void __launch_bounds__(kMaxBlockSites) schwarz_kernel(const SchwarzArg a) {
-  using T = typename Real<PREC>::T;
-  constexpr bool STAGE = PREC != P64;
+__global__ void __launch_bounds__(kMaxBlockSites, (SchwarzLayout<PREC, R>::kMinBlocks))
+    schwarz_kernel(const SchwarzArg a) {
+  using L = SchwarzLayout<PREC, R>;
+  using T = typename L::T;
+  using LIO = LinkIO<PREC, R>;
+  constexpr int RP = PREC == P64 ? P64 : P32;  // precision of the residual in smem
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* r_s = reinterpret_cast<T*>(smem_raw);
   const int nbs = a.b[0] * a.b[1] * a.b[2] * a.b[3];
-  float* l_s = reinterpret_cast<float*>(smem_raw + sizeof(T) * 24 * nbs);
-  float* c_s = l_s + 4 * 18 * nbs;
+  char* r_s = reinterpret_cast<char*>(smem_raw);
+  char* l_s = r_s + (size_t)L::kRSite * nbs;
+  char* c_s = l_s + (size_t)L::kLinkSite * nbs;
   __shared__ T red[kMaxBlockSites / 32][3];
   const int nwarp = (nbs + 31) / 32;
   const Geom& g = a.g;
@@ -87,117 +108,128 @@ __global__ void __launch_bounds__(kMaxBlockSites) schwarz_kernel(const SchwarzAr
   const int par = (x[0] + x[1] + x[2] + x[3]) & 1;
   const int cb = cb_index(g, x);
   const size_t hb = SpinorIO<PREC, 24>::half_bytes(Vh);
+  const char* clov_g = a.clover + par * CloverIO<PREC>::parity_bytes(Vh);
 
-  // stage r = b, the forward links and the clover
+  // neighbour local indices and boundary factors, -1 where the hop leaves the block
+  int nbr[8];
+  T nbc[8];
+  {
+    int stride = 1;
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu) {
+#pragma unroll
+      for (int dir = 0; dir < 2; ++dir) {
+        int ln = l[mu] + (dir == 0 ? 1 : -1);
+        T bc = (T)(-a.kappa);  // -kappa folded into the hop
+        bool ok = true;
+        if (ln == a.b[mu] || ln < 0) {
+          if (a.b[mu] != g.L[mu]) ok = false;
+          ln = dir == 0 ? 0 : a.b[mu] - 1;
+          if (mu == 3 && g.apbc) bc = -bc;
+        }
+        nbr[2 * mu + dir] = ok ? t + (ln - l[mu]) * stride : -1;
+        nbc[2 * mu + dir] = bc;
+      }
+      stride *= a.b[mu];
+    }
+  }
+
+  // stage r = b, and (FP32/FP16) the forward links and clover in storage format
   T xs[24];
   if (active) {
     T v[24];
     SpinorIO<PREC, 24>::load(a.in + par * hb, Vh, cb, v);
+    SpinorIO<RP, 24>::store(r_s, nbs, t, v);
 #pragma unroll
-    for (int k = 0; k < 24; ++k) {
-      r_s[k * nbs + t] = v[k];
-      xs[k] = 0;
-    }
-    if constexpr (STAGE) {
+    for (int k = 0; k < 24; ++k) xs[k] = 0;
+    if constexpr (L::kStage) {
+      constexpr int CB = LIO::kChunkBytes, NCH = LIO::kChunks;
 #pragma unroll
       for (int mu = 0; mu < 4; ++mu) {
-        Link<T> U;
-        LinkIO<PREC, R>::load(a.gauge, Vh, mu, par, cb, U);
+        const char* gp = a.gauge + (size_t)(mu * 2 + par) * link_plane_bytes(R, LIO::W, Vh);
+        char* sp = l_s + (size_t)mu * NCH * CB * nbs;
 #pragma unroll
-        for (int i = 0; i < 3; ++i)
-#pragma unroll
-          for (int j = 0; j < 3; ++j) {
-            l_s[(mu * 18 + 6 * i + 2 * j) * nbs + t] = U.m[i][j].r;
-            l_s[(mu * 18 + 6 * i + 2 * j + 1) * nbs + t] = U.m[i][j].i;
-          }
+        for (int k = 0; k < NCH; ++k)
+          copy_chunk<CB>(sp + ((size_t)k * nbs + t) * CB, gp + ((size_t)k * Vh + cb) * CB);
       }
-      float cv[72];
-      CloverIO<PREC>::load(a.clover + par * CloverIO<PREC>::parity_bytes(Vh), Vh, cb, cv);
+      constexpr int CCH = PREC == P32 ? 18 : 9;
 #pragma unroll
-      for (int k = 0; k < 72; ++k) c_s[k * nbs + t] = cv[k];
+      for (int k = 0; k < CCH; ++k)
+        copy_chunk<16>(c_s + ((size_t)k * nbs + t) * 16, clov_g + ((size_t)k * Vh + cb) * 16);
+      if constexpr (PREC == P16)
+        reinterpret_cast<float*>(c_s + (size_t)144 * nbs)[t] =
+            __ldg(reinterpret_cast<const float*>(clov_g + (size_t)144 * Vh) + cb);
     }
   }
   __syncthreads();
 
-  const T mk = -(T)a.kappa;
   for (int step = 0; step < a.steps; ++step) {
     T p[24];
     T red3[3] = {0, 0, 0};
     if (active) {
-      // p = Ahat r - kappa D_B r on this site
+      // p = Ahat r - kappa D_B r on this site: the clover part first
       C<T> acc[4][3];
+      {
+        T rv[24];
+        SpinorIO<RP, 24>::template load<false>(r_s, nbs, t, rv);
 #pragma unroll
-      for (int s = 0; s < 4; ++s)
+        for (int blk = 0; blk < 2; ++blk) {
+          T cl[36];
+          if constexpr (L::kStage) clover_block<PREC, false>((const char*)c_s, nbs, t, blk, cl);
+          else clover_block<PREC, true>(clov_g, Vh, cb, blk, cl);
+          C<T> in6[6], out6[6];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) acc[s][c] = C<T>{0, 0};
+          for (int k = 0; k < 6; ++k) in6[k] = C<T>{rv[12 * blk + 2 * k], rv[12 * blk + 2 * k + 1]};
+          herm6_mv<T>(cl, in6, out6);
+#pragma unroll
+          for (int k = 0; k < 6; ++k) acc[2 * blk + k / 3][k % 3] = out6[k];
+        }
+      }
 #pragma unroll
       for (int mu = 0; mu < 4; ++mu) {
 #pragma unroll
         for (int dir = 0; dir < 2; ++dir) {
-          int ln = l[mu] + (dir == 0 ? 1 : -1);
-          T bc = 1;
-          if (ln == a.b[mu] || ln < 0) {
-            if (a.b[mu] != g.L[mu]) continue;  // Dirichlet: hop leaves the block
-            ln = dir == 0 ? 0 : a.b[mu] - 1;
-            if (mu == 3 && g.apbc) bc = -1;
-          }
-          int lt = t;
-          {  // local index of the neighbour
-            int stride = 1;
-            for (int nu = 0; nu < mu; ++nu) stride *= a.b[nu];
-            lt = t + (ln - l[mu]) * stride;
-          }
+          const int lt = nbr[2 * mu + dir];
+          if (lt < 0) continue;  // Dirichlet: the hop leaves the block
           T psi[24];
-#pragma unroll
-          for (int k = 0; k < 24; ++k) psi[k] = r_s[k * nbs + lt];
+          SpinorIO<RP, 24>::template load<false>(r_s, nbs, lt, psi);
           Link<T> U;
-          const int ls = dir == 0 ? t : lt;  // forward: own link; backward: neighbour's
-          if constexpr (STAGE) {
-#pragma unroll
-            for (int i = 0; i < 3; ++i)
-#pragma unroll
-              for (int j = 0; j < 3; ++j)
-                U.m[i][j] = C<T>{l_s[(mu * 18 + 6 * i + 2 * j) * nbs + ls],
-                                 l_s[(mu * 18 + 6 * i + 2 * j + 1) * nbs + ls]};
+          const int ls = dir == 0 ? t : lt;  // forward: own link; backward: the neighbour's
+          if constexpr (L::kStage) {
+            LIO::template load_plane<false>(l_s + (size_t)mu * LIO::kChunks * LIO::kChunkBytes * nbs, nbs, ls, U);
           } else {
-            int y[4] = {x[0], x[1], x[2], x[3]};
-            y[mu] = bo[mu] + ln;
-            if (dir == 0) LinkIO<PREC, R>::load(a.gauge, Vh, mu, par, cb, U);
-            else LinkIO<PREC, R>::load(a.gauge, Vh, mu, 1 - par, cb_index(g, y), U);
+            if (dir == 0) {
+              LIO::load(a.gauge, Vh, mu, par, cb, U);
+            } else {
+              int y[4] = {x[0], x[1], x[2], x[3]};
+              int lb = l[mu] - 1;
+              y[mu] = bo[mu] + (lb < 0 ? a.b[mu] - 1 : lb);
+              LIO::load(a.gauge, Vh, mu, 1 - par, cb_index(g, y), U);
+            }
           }
           const T s = dir == 0 ? (T)-1 : (T)1;
-          const bool dag = dir == 1;
-          if (mu == 0) wilson_hop<0>(acc, psi, U, dag, s, bc);
-          if (mu == 1) wilson_hop<1>(acc, psi, U, dag, s, bc);
-          if (mu == 2) wilson_hop<2>(acc, psi, U, dag, s, bc);
-          if (mu == 3) wilson_hop<3>(acc, psi, U, dag, s, bc);
+          const T f = nbc[2 * mu + dir];
+          if (mu == 0) wilson_hop<0>(acc, psi, U, dir == 1, s, f);
+          if (mu == 1) wilson_hop<1>(acc, psi, U, dir == 1, s, f);
+          if (mu == 2) wilson_hop<2>(acc, psi, U, dir == 1, s, f);
+          if (mu == 3) wilson_hop<3>(acc, psi, U, dir == 1, s, f);
         }
       }
-      C<T> rv[12], av[12];
-#pragma unroll
-      for (int k = 0; k < 12; ++k) rv[k] = C<T>{r_s[(2 * k) * nbs + t], r_s[(2 * k + 1) * nbs + t]};
-      if constexpr (STAGE) {
-        T cl[72];
-#pragma unroll
-        for (int k = 0; k < 72; ++k) cl[k] = c_s[k * nbs + t];
-        herm6_mv<T>(cl, rv, av);
-        herm6_mv<T>(cl + 36, rv + 6, av + 6);
-      } else {
-        apply_clover_site<PREC, T>(a.clover + par * CloverIO<PREC>::parity_bytes(Vh), Vh, cb, rv, av);
-      }
+      T rv[24];
+      SpinorIO<RP, 24>::template load<false>(r_s, nbs, t, rv);
 #pragma unroll
       for (int s = 0; s < 4; ++s)
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-          p[6 * s + 2 * c] = fma(mk, acc[s][c].r, av[3 * s + c].r);
-          p[6 * s + 2 * c + 1] = fma(mk, acc[s][c].i, av[3 * s + c].i);
+          p[6 * s + 2 * c] = acc[s][c].r;
+          p[6 * s + 2 * c + 1] = acc[s][c].i;
         }
       // (p, r) and (p, p)
 #pragma unroll
       for (int k = 0; k < 12; ++k) {
-        T pr = p[2 * k], pi = p[2 * k + 1];
-        red3[0] = fma(pr, rv[k].r, red3[0]); red3[0] = fma(pi, rv[k].i, red3[0]);
-        red3[1] = fma(pr, rv[k].i, red3[1]); red3[1] = fma(-pi, rv[k].r, red3[1]);
+        T pr = p[2 * k], pi = p[2 * k + 1], rr = rv[2 * k], ri = rv[2 * k + 1];
+        red3[0] = fma(pr, rr, red3[0]); red3[0] = fma(pi, ri, red3[0]);
+        red3[1] = fma(pr, ri, red3[1]); red3[1] = fma(-pi, rr, red3[1]);
         red3[2] = fma(pr, pr, red3[2]); red3[2] = fma(pi, pi, red3[2]);
       }
     }
@@ -208,33 +240,45 @@ __global__ void __launch_bounds__(kMaxBlockSites) schwarz_kernel(const SchwarzAr
       ai = red3[1] / red3[2];
     }
     if (active) {
+      T rv[24];
+      SpinorIO<RP, 24>::template load<false>(r_s, nbs, t, rv);
 #pragma unroll
       for (int k = 0; k < 12; ++k) {
-        T rr = r_s[(2 * k) * nbs + t], ri = r_s[(2 * k + 1) * nbs + t];
+        T rr = rv[2 * k], ri = rv[2 * k + 1];
         xs[2 * k] += ar * rr - ai * ri;
         xs[2 * k + 1] += ar * ri + ai * rr;
-        r_s[(2 * k) * nbs + t] = rr - (ar * p[2 * k] - ai * p[2 * k + 1]);
-        r_s[(2 * k + 1) * nbs + t] = ri - (ar * p[2 * k + 1] + ai * p[2 * k]);
+        rv[2 * k] = rr - (ar * p[2 * k] - ai * p[2 * k + 1]);
+        rv[2 * k + 1] = ri - (ar * p[2 * k + 1] + ai * p[2 * k]);
       }
+      SpinorIO<RP, 24>::store(r_s, nbs, t, rv);
     }
     __syncthreads();
   }
   if (active) SpinorIO<PREC, 24>::store(a.out + par * hb, Vh, cb, xs);
 }
 
+template <int PREC, int R>
+static int schwarz_launch(const SchwarzArg& a, int nblocks, int nbs, cudaStream_t st) {
+  using L = SchwarzLayout<PREC, R>;
+  const size_t smem = (size_t)L::kSite * nbs;
+  const int threads = ((nbs + 31) / 32) * 32;
+  auto kern = schwarz_kernel<PREC, R>;
+  static bool configured = false;  // the attribute is per kernel, set once
+  if (!configured) {
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)((size_t)L::kSite * kMaxBlockSites)) != cudaSuccess)
+      return DIRAC_ERR_CUDA;
+    configured = true;
+  }
+  kern<<<nblocks, threads, smem, st>>>(a);
+  return cudaGetLastError() == cudaSuccess ? DIRAC_OK : DIRAC_ERR_CUDA;
+}
+
 template <int PREC>
 static int schwarz_prec(int recon, const SchwarzArg& a, int nblocks, int nbs, cudaStream_t st) {
-  size_t smem = sizeof(typename Real<PREC>::T) * 24 * nbs;
-  if (PREC != P64) smem += sizeof(float) * (4 * 18 + 72) * nbs;
-  int threads = ((nbs + 31) / 32) * 32;
-  auto launch = [&](auto kern) {
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    kern<<<nblocks, threads, smem, st>>>(a);
-  };
-  if (recon == 18) launch(schwarz_kernel<PREC, 18>);
-  else if (recon == 12) launch(schwarz_kernel<PREC, 12>);
-  else launch(schwarz_kernel<PREC, 8>);
-  return cudaGetLastError() == cudaSuccess ? DIRAC_OK : DIRAC_ERR_CUDA;
+  if (recon == 18) return schwarz_launch<PREC, 18>(a, nblocks, nbs, st);
+  if (recon == 12) return schwarz_launch<PREC, 12>(a, nblocks, nbs, st);
+  return schwarz_launch<PREC, 8>(a, nblocks, nbs, st);
 }
 
 int launch_schwarz(int prec, int recon, char* out, const char* in, const char* gauge,
