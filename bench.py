@@ -381,6 +381,41 @@ def measure_wilson_rows(lat, dirac, fields, precs, stream, peak):
     return out
 
 
+MS_SHIFTS = (0.0, 0.0005, 0.005, 0.05)
+
+
+def multishift_bench(lat, dirac, b, torch):
+    """Eq. 4 with 4 shifts, Sec. 8.2 strategy (FP32 multi-shift CG, then mixed FP64/FP32
+    refinement of each solution) vs one mixed FP64/FP32 CG per shift from zero."""
+    xs = [lat.new_field(dirac.F64, 0) for _ in MS_SHIFTS]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    st = lat.solve_multishift(xs, b, list(MS_SHIFTS), dirac.CG_EVEN_NORMAL, tol=1e-10,
+                              max_iter=6000, delta=0.1, prec_sloppy=dirac.F32, raise_on_error=False)
+    torch.cuda.synchronize()
+    t_ms = time.perf_counter() - t0
+    out = {"shifts": list(MS_SHIFTS), "status": st["status"], "seconds": round(t_ms, 3),
+           "multishift_iters": st["multishift"]["iters"],
+           "multishift_seconds": round(st["multishift"]["seconds"], 3),
+           "refine_iters": [r["iters"] for r in st["refine"]],
+           "true_rel_resid": [float(f"{r['true_rel_resid']:.3g}") for r in st["refine"]]}
+    seq_t, seq_it = 0.0, []
+    for sgm, x in zip(MS_SHIFTS, xs):
+        x.zero_()
+        # a single-shift call is one mixed FP64/FP32 CG on (M^dagger M + sigma) from zero
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        r = lat.solve_multishift([x], b, [sgm], dirac.CG_EVEN_NORMAL, tol=1e-10, max_iter=6000,
+                                 delta=0.1, prec_sloppy=dirac.F32, raise_on_error=False)
+        torch.cuda.synchronize()
+        seq_t += time.perf_counter() - t1
+        seq_it.append(r["multishift"]["iters"] + r["refine"][0]["iters"])
+    out["sequential_mixed_seconds"] = round(seq_t, 3)
+    out["sequential_mixed_iters"] = seq_it
+    out["speedup_vs_sequential_mixed"] = round(seq_t / t_ms, 3) if t_ms > 0 else None
+    return out
+
+
 def measure_asqtad(dirac, synth, dev, stream, peak, do_solve, dims):
     """Asqtad parity dslash and even-site normal operator (48^3x144, m = 0.01), and
     CG on (M^dagger M)_ee, mixed FP64/FP32 vs plain FP64. (An FP16 Krylov space
@@ -422,6 +457,7 @@ def measure_asqtad(dirac, synth, dev, stream, peak, do_solve, dims):
             if sol[tag]["status"] == "OK" and sol["cg_f64"]["status"] == "OK":
                 sol[tag + "_speedup_vs_f64"] = round(sol["cg_f64"]["seconds"] / sol[tag]["seconds"], 3)
         res["solve_cg_even_m0.01"] = sol
+        res["solve_multishift_m0.01"] = multishift_bench(lat, dirac, b, torch)
     lat.close()
     return res
 

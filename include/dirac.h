@@ -202,6 +202,19 @@ typedef struct {
 int solve(dirac_ctx* ctx, void* x, const void* b, const dirac_solver_params* params,
           dirac_solver_stats* stats, void* stream);
 
+/* Multi-shift solve of Eq. 4, (M^dagger M + sigma_j) x_j = b for j < nshift (1..16,
+ * sigma_j >= 0), the strategy of Sec. 8.2: a multi-shift CG in params->prec_sloppy
+ * builds one Krylov space for every shift (down to a relative residual of 1e-6 in
+ * FP32, 1e-3 in FP16), then each x_j is refined by mixed-precision CG on its own
+ * system, warm-started, with reliable updates every params->delta, to params->tol.
+ * params->alg: DIRAC_SOLVER_CG_EVEN_NORMAL (asqtad, even half-fields) or
+ * DIRAC_SOLVER_CG_NORMAL (full fields). x: nshift distinct FP64 device fields
+ * (outputs); b: FP64 device field. stats (may be NULL): nshift + 1 entries, [0] the
+ * multi-shift stage, [1 + j] the refinement of shift j (true_rel_resid of shift j).
+ * Returns DIRAC_ERR_NOT_CONVERGED if some refinement ran out of iterations. */
+int solve_multishift(dirac_ctx* ctx, void* const* x, const void* b, const double* shifts, int nshift,
+                     const dirac_solver_params* params, dirac_solver_stats* stats, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

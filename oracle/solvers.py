@@ -178,3 +178,71 @@ def gcr(M, K, b, tol, max_iter, k_max, delta, x0=None):
 def true_residual(M, x, b):
     """||b - M x|| / ||b|| in float64."""
     return float(np.sqrt(norm2(b - M(x)) / norm2(b)))
+
+
+# ---------------------------------------------------------------------------
+# Multi-shift CG (Sec. 3.1, Eq. 4; Sec. 8.2)
+# ---------------------------------------------------------------------------
+
+def multishift_cg(A, b, shifts, tol, max_iter):
+    """Solve (A + sigma_i) x_i = b for every shift with one Krylov space (Eq. 4), A
+    Hermitian positive definite, all sigma_i >= 0.
+
+    The base system is the smallest shift sigma_0 (the least well conditioned one),
+    solved by plain CG with A' = A + sigma_0. Its residuals r_k and the residuals of a
+    shifted system A' + s (s = sigma_i - sigma_0) are collinear, r^i_k = zeta_k r_k,
+    because both lie in the same Krylov space and are orthogonal to it. Writing the
+    CG three-term recurrence of both systems and equating coefficients gives
+        zeta_{k+1} = zeta_k zeta_{k-1} a_{k-1}
+                     / (a_{k-1} zeta_{k-1} (1 + s a_k) + a_k b_{k-1} (zeta_{k-1} - zeta_k)),
+        a^i_k = a_k zeta_{k+1} / zeta_k,     b^i_k = b_k (zeta_{k+1} / zeta_k)^2,
+        x^i += a^i_k p^i_k,   p^i_{k+1} = zeta_{k+1} r_{k+1} + b^i_k p^i_k,
+    with zeta_{-1} = zeta_0 = 1, a_{-1} = 1, b_{-1} = 0 and p^i_0 = b.
+    A shifted system whose residual ||zeta^i r|| <= tol ||b|| is converged and is no
+    longer updated (its zeta would underflow). Stops when the base system converges.
+    Returns (list of x_i in the order of `shifts`, info)."""
+    shifts = list(shifts)
+    order = sorted(range(len(shifts)), key=lambda i: shifts[i])
+    s0 = shifts[order[0]]
+    n = len(shifts)
+    x = [np.zeros_like(b) for _ in range(n)]
+    p = [b.copy() for _ in range(n)]
+    r = b.copy()
+    rr = norm2(r)
+    bb = norm2(b)
+    zeta = np.ones(n)
+    zeta_prev = np.ones(n)
+    a_prev, b_prev = 1.0, 0.0
+    info = {"iters": 0}
+    active = [True] * n
+    for k in range(max_iter):
+        for i in range(n):
+            if active[i] and zeta[i] ** 2 * rr <= tol * tol * bb:
+                active[i] = False
+        if not any(active):
+            break
+        i0 = order[0]
+        Ap = A(p[i0]) + s0 * p[i0]
+        a = rr / dot(p[i0], Ap).real
+        r = r - a * Ap
+        rr_new = norm2(r)
+        bk = rr_new / rr
+        for i in range(n):
+            if not active[i]:
+                continue
+            s = shifts[i] - s0
+            if i == i0:
+                z_next = 1.0
+            else:
+                den = a_prev * zeta_prev[i] * (1.0 + s * a) + a * b_prev * (zeta_prev[i] - zeta[i])
+                z_next = zeta[i] * zeta_prev[i] * a_prev / den
+            ai = a * z_next / zeta[i]
+            bi = bk * (z_next / zeta[i]) ** 2
+            x[i] = x[i] + ai * p[i]
+            p[i] = z_next * r + bi * p[i]
+            zeta_prev[i], zeta[i] = zeta[i], z_next
+        a_prev, b_prev = a, bk
+        rr = rr_new
+        info["iters"] = k + 1
+    info["zeta"] = zeta.copy()
+    return x, info

@@ -110,27 +110,31 @@ int stag_hop(dirac_ctx* c, char* out, const char* in, const char* x, int parity,
 
 // A x for the operator family; `which`: 0 = M, 1 = M^dagger, 2 = M^dagger M.
 // parity: FULL, or EVEN/ODD (hopping block for M/M^dagger; (M^dagger M)_pp for asqtad).
-int apply_op(dirac_ctx* c, char* out, const char* in, int parity, int prec, int which, cudaStream_t st) {
+int apply_op(dirac_ctx* c, char* out, const char* in, int parity, int prec, int which, cudaStream_t st,
+             double shift) {
   const bool wil = c->p.kind == DIRAC_WILSON_CLOVER;
   const size_t hb = spinor_half_bytes(prec, c->nr, c->Vh);
   int rc;
-  if (which == 2) {
+  if (which == 2) {  // M^dagger M + shift
     if ((rc = ensure_tmp(c, prec))) return rc;
     char* t = c->tmp[prec];
     if (wil) {
       if (parity >= 0) return set_err(c, DIRAC_ERR_UNSUPPORTED, "Wilson normal operator is full-lattice only");
       if ((rc = wilson_M(c, t, in, prec, false, st))) return rc;
-      return wilson_M(c, out, t, prec, true, st);
+      if ((rc = wilson_M(c, out, t, prec, true, st))) return rc;
+      if (shift != 0.0)
+        return blas_axpby(c->blas, cval(shift), field_ref(c, in, prec, -1), cval(1), field_ref(c, out, prec, -1), st);
+      return DIRAC_OK;
     }
-    const double m = c->p.mass;
+    const double m2 = c->p.mass * c->p.mass + shift;
     if (parity >= 0) {  // (M^dagger M)_pp = m^2 - 1/4 D_{p,1-p} D_{1-p,p}
       if ((rc = stag_hop(c, t, in, nullptr, 1 - parity, prec, 0.0, 1.0, st))) return rc;
-      return stag_hop(c, out, t, in, parity, prec, m * m, -0.25, st);
+      return stag_hop(c, out, t, in, parity, prec, m2, -0.25, st);
     }
     for (int p = 0; p < 2; ++p)  // t = D in
       if ((rc = stag_hop(c, t + p * hb, in + (1 - p) * hb, nullptr, p, prec, 0.0, 1.0, st))) return rc;
     for (int p = 0; p < 2; ++p)  // out = m^2 in - 1/4 D t
-      if ((rc = stag_hop(c, out + p * hb, t + (1 - p) * hb, in + p * hb, p, prec, m * m, -0.25, st))) return rc;
+      if ((rc = stag_hop(c, out + p * hb, t + (1 - p) * hb, in + p * hb, p, prec, m2, -0.25, st))) return rc;
     return DIRAC_OK;
   }
   const bool dag = which == 1;
@@ -209,16 +213,18 @@ int dirac_create(const dirac_params* params, dirac_ctx** out) {
 
 int dirac_destroy(dirac_ctx* c) {
   if (!c) return DIRAC_ERR_ARG;
-  for (int q = 0; q < 3; ++q) {
-    for (char* p : {c->gauge[q], c->fat[q], c->clover[q], c->tmp[q], c->tmp2[q]})
-      if (p) cudaFree(p);
-  }
-  for (int i = 0; i < 48; ++i)
-    if (c->work[i]) cudaFree(c->work[i]);
-  if (c->staging) cudaFree(c->staging);
+  bool ok = true;
+  auto fr = [&](void* p) { if (p && cudaFree(p) != cudaSuccess) ok = false; };
+  for (int q = 0; q < 3; ++q)
+    for (char* p : {c->gauge[q], c->fat[q], c->clover[q], c->tmp[q], c->tmp2[q]}) fr(p);
+  for (int i = 0; i < 48; ++i) fr(c->work[i]);
+  fr(c->staging);
+  fr(c->dscal);
+  if (c->hmirror && cudaFreeHost(c->hmirror) != cudaSuccess) ok = false;
   blas_destroy(c->blas);
   delete c;
-  return DIRAC_OK;
+  cudaGetLastError();  // leave no pending error behind for later contexts
+  return ok ? DIRAC_OK : DIRAC_ERR_CUDA;
 }
 
 const char* dirac_last_error(const dirac_ctx* c) { return c ? c->err.c_str() : "null context"; }
@@ -365,8 +371,8 @@ int dirac_caxpy_norm(dirac_ctx* c, double ar, double ai, const void* x, void* y,
                      dirac_parity parity, double* result, void* stream) {
   if (!c || !x || !y || !result || x == y || !valid_prec(prec))
     return set_err(c, DIRAC_ERR_ARG, "bad caxpy_norm arguments");
-  return blas_rc(c, blas_caxpy_norm(c->blas, ar, ai, field_ref(c, x, prec, parity), field_ref(c, y, prec, parity),
-                                    result, (cudaStream_t)stream));
+  return blas_rc(c, blas_caxpy_norm(c->blas, cval(ar, ai), field_ref(c, x, prec, parity),
+                                    field_ref(c, y, prec, parity), result, (cudaStream_t)stream));
 }
 
 int dirac_convert(dirac_ctx* c, void* dst, dirac_prec dprec, const void* src, dirac_prec sprec,

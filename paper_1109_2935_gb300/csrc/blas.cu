@@ -94,24 +94,31 @@ __device__ __forceinline__ void site_store(const FieldRef& f, int s, const T v[N
 }
 
 // ---------------------------------------------------------------- operations
-// Each op: void operator()(int site, double acc[3]) const.
+// Each op: void operator()(int site, double acc[3]) const. Complex coefficients are
+// `Cf`: a host value, or (scale x) a device value that an earlier reduction or a
+// solver's scalar kernel wrote, so solvers need not bring scalars to the host.
+template <typename T>
+__device__ __forceinline__ void cf_get(const Cf& c, T& r, T& i) {
+  if (c.p) {
+    r = (T)(c.s * c.p[0]);
+    i = (T)(c.s * c.p[1]);
+  } else {
+    r = (T)c.r;
+    i = (T)c.i;
+  }
+}
+
 template <int NR, typename T> struct OpCopy {
   FieldRef d, s;
   __device__ void operator()(int i, double*) const { T v[NR]; site_load<NR>(s, i, v); site_store<NR>(d, i, v); }
 };
-template <int NR, typename T> struct OpZero {
-  FieldRef x;
-  __device__ void operator()(int i, double*) const {
-    T v[NR];
-#pragma unroll
-    for (int k = 0; k < NR; ++k) v[k] = 0;
-    site_store<NR>(x, i, v);
-  }
-};
 // y = a x + b y
 template <int NR, typename T> struct OpAxpby {
-  FieldRef x, y; T ar, ai, br, bi;
+  FieldRef x, y; Cf a, b;
   __device__ void operator()(int i, double*) const {
+    T ar, ai, br, bi;
+    cf_get(a, ar, ai);
+    cf_get(b, br, bi);
     T u[NR], v[NR];
     site_load<NR>(x, i, u); site_load<NR>(y, i, v);
 #pragma unroll
@@ -123,33 +130,22 @@ template <int NR, typename T> struct OpAxpby {
     site_store<NR>(y, i, v);
   }
 };
-// z = x + a y
-template <int NR, typename T> struct OpXpayTo {
-  FieldRef x, y, z; T ar, ai;
+// p = r + b p + c v   (BiCGstab direction update with b = beta, c = -beta omega)
+template <int NR, typename T> struct OpPUpdate {
+  FieldRef r, v, p; Cf b, c;
   __device__ void operator()(int i, double*) const {
-    T u[NR], v[NR];
-    site_load<NR>(x, i, u); site_load<NR>(y, i, v);
+    T br, bi, cr, ci;
+    cf_get(b, br, bi);
+    cf_get(c, cr, ci);
+    T ur[NR], uv[NR], up[NR];
+    site_load<NR>(r, i, ur); site_load<NR>(v, i, uv); site_load<NR>(p, i, up);
 #pragma unroll
     for (int k = 0; k < NR / 2; ++k) {
-      T yr = v[2 * k], yi = v[2 * k + 1];
-      u[2 * k] += ar * yr - ai * yi;
-      u[2 * k + 1] += ar * yi + ai * yr;
+      T pr = up[2 * k], pi = up[2 * k + 1], vr = uv[2 * k], vi = uv[2 * k + 1];
+      up[2 * k] = ur[2 * k] + br * pr - bi * pi + cr * vr - ci * vi;
+      up[2 * k + 1] = ur[2 * k + 1] + br * pi + bi * pr + cr * vi + ci * vr;
     }
-    site_store<NR>(z, i, u);
-  }
-};
-// y += a x + b z
-template <int NR, typename T> struct OpAxpbzAdd {
-  FieldRef x, z, y; T ar, ai, br, bi;
-  __device__ void operator()(int i, double*) const {
-    T u[NR], w[NR], v[NR];
-    site_load<NR>(x, i, u); site_load<NR>(z, i, w); site_load<NR>(y, i, v);
-#pragma unroll
-    for (int k = 0; k < NR / 2; ++k) {
-      v[2 * k] += ar * u[2 * k] - ai * u[2 * k + 1] + br * w[2 * k] - bi * w[2 * k + 1];
-      v[2 * k + 1] += ar * u[2 * k + 1] + ai * u[2 * k] + br * w[2 * k + 1] + bi * w[2 * k];
-    }
-    site_store<NR>(y, i, v);
+    site_store<NR>(p, i, up);
   }
 };
 template <int NR, typename T> struct OpNorm2 {
@@ -180,10 +176,29 @@ template <int NR, typename T> struct OpCdotNorm {
     acc[0] += (double)re; acc[1] += (double)im; acc[2] += (double)nn;
   }
 };
+template <int NR, typename T>
+__device__ __forceinline__ void acc_norm_dot(const T* v, const FieldRef* w, int i, double* acc, bool dot) {
+  T nn = 0;
+#pragma unroll
+  for (int k = 0; k < NR; ++k) nn = fma(v[k], v[k], nn);
+  acc[0] += (double)nn;
+  if (dot) {
+    T ww[NR], re = 0, im = 0;
+    site_load<NR>(*w, i, ww);
+#pragma unroll
+    for (int k = 0; k < NR / 2; ++k) {
+      re = fma(ww[2 * k], v[2 * k], re); re = fma(ww[2 * k + 1], v[2 * k + 1], re);
+      im = fma(ww[2 * k], v[2 * k + 1], im); im = fma(-ww[2 * k + 1], v[2 * k], im);
+    }
+    acc[1] += (double)re; acc[2] += (double)im;
+  }
+}
 // y += a x ; ||y||^2, (w, y)
 template <int NR, typename T, bool DOT> struct OpCaxpyNorm {
-  FieldRef x, y, w; T ar, ai;
+  FieldRef x, y, w; Cf a;
   __device__ void operator()(int i, double* acc) const {
+    T ar, ai;
+    cf_get(a, ar, ai);
     T u[NR], v[NR];
     site_load<NR>(x, i, u); site_load<NR>(y, i, v);
 #pragma unroll
@@ -194,30 +209,75 @@ template <int NR, typename T, bool DOT> struct OpCaxpyNorm {
     }
     site_store<NR>(y, i, v);
     if (y.prec == P16) site_load<NR>(y, i, v);  // reduce what is stored
-    T nn = 0;
-#pragma unroll
-    for (int k = 0; k < NR; ++k) nn = fma(v[k], v[k], nn);
-    acc[0] += (double)nn;
-    if (DOT) {
-      T ww[NR], re = 0, im = 0;
-      site_load<NR>(w, i, ww);
-#pragma unroll
-      for (int k = 0; k < NR / 2; ++k) {
-        re = fma(ww[2 * k], v[2 * k], re); re = fma(ww[2 * k + 1], v[2 * k + 1], re);
-        im = fma(ww[2 * k], v[2 * k + 1], im); im = fma(-ww[2 * k + 1], v[2 * k], im);
-      }
-      acc[1] += (double)re; acc[2] += (double)im;
-    }
+    acc_norm_dot<NR, T>(v, &w, i, acc, DOT);
   }
 };
-// x *= s ; (x, y)
-template <int NR, typename T> struct OpScaleCdot {
-  FieldRef x, y; T s;
+// xs += a p + b s ;  s += c t (s becomes r) ; ||r||^2, (w, r)     (BiCGstab)
+template <int NR, typename T> struct OpBicgXR {
+  FieldRef p, s, t, xs, w; Cf a, b, c;
   __device__ void operator()(int i, double* acc) const {
+    T ar, ai, br, bi, cr, ci;
+    cf_get(a, ar, ai);
+    cf_get(b, br, bi);
+    cf_get(c, cr, ci);
+    T up[NR], us[NR], ux[NR];
+    site_load<NR>(p, i, up); site_load<NR>(s, i, us); site_load<NR>(xs, i, ux);
+#pragma unroll
+    for (int k = 0; k < NR / 2; ++k) {
+      ux[2 * k] += ar * up[2 * k] - ai * up[2 * k + 1] + br * us[2 * k] - bi * us[2 * k + 1];
+      ux[2 * k + 1] += ar * up[2 * k + 1] + ai * up[2 * k] + br * us[2 * k + 1] + bi * us[2 * k];
+    }
+    site_store<NR>(xs, i, ux);
+    T ut[NR];
+    site_load<NR>(t, i, ut);
+#pragma unroll
+    for (int k = 0; k < NR / 2; ++k) {
+      T tr = ut[2 * k], ti = ut[2 * k + 1];
+      us[2 * k] += cr * tr - ci * ti;
+      us[2 * k + 1] += cr * ti + ci * tr;
+    }
+    site_store<NR>(s, i, us);
+    if (s.prec == P16) site_load<NR>(s, i, us);
+    acc_norm_dot<NR, T>(us, &w, i, acc, true);
+  }
+};
+// xs += a p ; r += c Ap ; ||r||^2     (CG, c = -a)
+template <int NR, typename T> struct OpCgUpdate {
+  FieldRef p, Ap, xs, r; Cf a, c;
+  __device__ void operator()(int i, double* acc) const {
+    T ar, ai, cr, ci;
+    cf_get(a, ar, ai);
+    cf_get(c, cr, ci);
+    T up[NR], ux[NR];
+    site_load<NR>(p, i, up); site_load<NR>(xs, i, ux);
+#pragma unroll
+    for (int k = 0; k < NR / 2; ++k) {
+      ux[2 * k] += ar * up[2 * k] - ai * up[2 * k + 1];
+      ux[2 * k + 1] += ar * up[2 * k + 1] + ai * up[2 * k];
+    }
+    site_store<NR>(xs, i, ux);
+    T ua[NR], ur[NR];
+    site_load<NR>(Ap, i, ua); site_load<NR>(r, i, ur);
+#pragma unroll
+    for (int k = 0; k < NR / 2; ++k) {
+      ur[2 * k] += cr * ua[2 * k] - ci * ua[2 * k + 1];
+      ur[2 * k + 1] += cr * ua[2 * k + 1] + ci * ua[2 * k];
+    }
+    site_store<NR>(r, i, ur);
+    if (r.prec == P16) site_load<NR>(r, i, ur);
+    acc_norm_dot<NR, T>(ur, nullptr, i, acc, false);
+  }
+};
+// x *= s (real part of the coefficient) ; (x, y)
+template <int NR, typename T> struct OpScaleCdot {
+  FieldRef x, y; Cf s;
+  __device__ void operator()(int i, double* acc) const {
+    T sr, si;
+    cf_get(s, sr, si);
     T u[NR], v[NR];
     site_load<NR>(x, i, u);
 #pragma unroll
-    for (int k = 0; k < NR; ++k) u[k] *= s;
+    for (int k = 0; k < NR; ++k) u[k] *= sr;
     site_store<NR>(x, i, u);
     if (x.prec == P16) site_load<NR>(x, i, u);
     site_load<NR>(y, i, v);
@@ -246,7 +306,7 @@ template <int NR, typename T> struct OpXmyNorm {
     acc[0] += (double)nn;
   }
 };
-struct MultiCoef { FieldRef x[kMaxMulti]; double cr[kMaxMulti], ci[kMaxMulti]; int n; };
+struct MultiCoef { FieldRef x[kMaxMulti]; Cf c[kMaxMulti]; int n; };
 template <int NR, typename T> struct OpMultiCaxpy {
   MultiCoef m; FieldRef y;
   __device__ void operator()(int i, double*) const {
@@ -255,7 +315,8 @@ template <int NR, typename T> struct OpMultiCaxpy {
     for (int j = 0; j < m.n; ++j) {
       T u[NR];
       site_load<NR>(m.x[j], i, u);
-      const T cr = (T)m.cr[j], ci = (T)m.ci[j];
+      T cr, ci;
+      cf_get(m.c[j], cr, ci);
 #pragma unroll
       for (int k = 0; k < NR / 2; ++k) {
         v[2 * k] += cr * u[2 * k] - ci * u[2 * k + 1];
@@ -263,6 +324,32 @@ template <int NR, typename T> struct OpMultiCaxpy {
       }
     }
     site_store<NR>(y, i, v);
+  }
+};
+
+// Multi-shift CG (Eq. 4) update of every still-active shifted system j in one pass:
+//   x_j += a_j p_j ;  p_j = z_j r + b_j p_j
+// with (a_j, z_j, b_j, active_j) = coef[4 j .. 4 j + 3] written on the device.
+struct ShiftFields { FieldRef x[kMaxMulti], p[kMaxMulti]; int n; };
+template <int NR, typename T> struct OpMultiShift {
+  ShiftFields f; FieldRef r; const double* coef;
+  __device__ void operator()(int i, double*) const {
+    T ur[NR];
+    site_load<NR>(r, i, ur);
+    for (int j = 0; j < f.n; ++j) {
+      if (coef[4 * j + 3] == 0.0) continue;  // converged: no longer updated
+      const T a = (T)coef[4 * j], z = (T)coef[4 * j + 1], b = (T)coef[4 * j + 2];
+      T up[NR], ux[NR];
+      site_load<NR>(f.p[j], i, up);
+      site_load<NR>(f.x[j], i, ux);
+#pragma unroll
+      for (int k = 0; k < NR; ++k) {
+        ux[k] = fma(a, up[k], ux[k]);
+        up[k] = fma(b, up[k], z * ur[k]);
+      }
+      site_store<NR>(f.x[j], i, ux);
+      site_store<NR>(f.p[j], i, up);
+    }
   }
 };
 
@@ -352,13 +439,14 @@ static int run_map(Blas* b, const Op& op, int n, cudaStream_t st) {
 }
 
 template <class Op>
-static int run_reduce(Blas* b, const Op& op, int n, double* out, int nout, cudaStream_t st) {
+static int run_reduce(Blas* b, const Op& op, int n, double* out, int nout, cudaStream_t st,
+                      double* dres) {
   int grid = (n + kThreads - 1) / kThreads;
   if (grid > kRedBlocks) grid = kRedBlocks;
   if (grid < 1) grid = 1;
-  blas_reduce_kernel<Op><<<grid, kThreads, 0, st>>>(op, n, b->partials, b->ticket, b->dev_res);
+  blas_reduce_kernel<Op><<<grid, kThreads, 0, st>>>(op, n, b->partials, b->ticket, dres ? dres : b->dev_res);
   int rc = check(b, "blas reduce kernel");
-  if (rc) return rc;
+  if (rc || dres) return rc;  // device-resident result: no synchronisation
   cudaError_t e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) {
     b->err = std::string("reduction sync: ") + cudaGetErrorString(e);
@@ -387,61 +475,79 @@ int blas_zero(Blas* b, const FieldRef& x, cudaStream_t st) {
   if (cudaMemsetAsync(x.p, 0, x.hb * x.npar, st) != cudaSuccess) return check(b, "memset");
   return DIRAC_OK;
 }
-int blas_axpby(Blas* b, double ar, double ai, const FieldRef& x, double br, double bi,
-               const FieldRef& y, cudaStream_t st) {
-  DISPATCH(y.nr, any64({&x, &y}),
-           return run_map(b, (OpAxpby<NR, T>{x, y, (T)ar, (T)ai, (T)br, (T)bi}), nsites(y), st));
+int blas_axpby(Blas* b, Cf a, const FieldRef& x, Cf bb, const FieldRef& y, cudaStream_t st) {
+  DISPATCH(y.nr, any64({&x, &y}), return run_map(b, (OpAxpby<NR, T>{x, y, a, bb}), nsites(y), st));
 }
-int blas_xpay_to(Blas* b, const FieldRef& x, double ar, double ai, const FieldRef& y,
-                 const FieldRef& z, cudaStream_t st) {
-  DISPATCH(z.nr, any64({&x, &y, &z}),
-           return run_map(b, (OpXpayTo<NR, T>{x, y, z, (T)ar, (T)ai}), nsites(z), st));
+int blas_pupdate(Blas* b, const FieldRef& r, Cf beta, Cf c, const FieldRef& v, const FieldRef& p,
+                 cudaStream_t st) {
+  DISPATCH(p.nr, any64({&r, &v, &p}), return run_map(b, (OpPUpdate<NR, T>{r, v, p, beta, c}), nsites(p), st));
 }
-int blas_axpbz_add(Blas* b, double ar, double ai, const FieldRef& x, double br, double bi,
-                   const FieldRef& z, const FieldRef& y, cudaStream_t st) {
-  DISPATCH(y.nr, any64({&x, &z, &y}),
-           return run_map(b, (OpAxpbzAdd<NR, T>{x, z, y, (T)ar, (T)ai, (T)br, (T)bi}), nsites(y), st));
+int blas_norm2(Blas* b, const FieldRef& x, double* out, cudaStream_t st, double* dres) {
+  DISPATCH(x.nr, any64({&x}), return run_reduce(b, (OpNorm2<NR, T>{x}), nsites(x), out, 1, st, dres));
 }
-int blas_norm2(Blas* b, const FieldRef& x, double* out, cudaStream_t st) {
-  DISPATCH(x.nr, any64({&x}), return run_reduce(b, (OpNorm2<NR, T>{x}), nsites(x), out, 1, st));
-}
-int blas_cdot(Blas* b, const FieldRef& x, const FieldRef& y, double out[2], cudaStream_t st) {
+int blas_cdot(Blas* b, const FieldRef& x, const FieldRef& y, double out[2], cudaStream_t st, double* dres) {
   DISPATCH(x.nr, any64({&x, &y}),
-           return run_reduce(b, (OpCdotNorm<NR, T>{x, y}), nsites(x), out, 2, st));
+           return run_reduce(b, (OpCdotNorm<NR, T>{x, y}), nsites(x), out, 2, st, dres));
 }
-int blas_cdot_norm(Blas* b, const FieldRef& x, const FieldRef& y, double out[3], cudaStream_t st) {
+int blas_cdot_norm(Blas* b, const FieldRef& x, const FieldRef& y, double out[3], cudaStream_t st,
+                   double* dres) {
   DISPATCH(x.nr, any64({&x, &y}),
-           return run_reduce(b, (OpCdotNorm<NR, T>{x, y}), nsites(x), out, 3, st));
+           return run_reduce(b, (OpCdotNorm<NR, T>{x, y}), nsites(x), out, 3, st, dres));
 }
-int blas_caxpy_norm(Blas* b, double ar, double ai, const FieldRef& x, const FieldRef& y,
-                    double* out, cudaStream_t st) {
+int blas_caxpy_norm(Blas* b, Cf a, const FieldRef& x, const FieldRef& y, double* out, cudaStream_t st,
+                    double* dres) {
   DISPATCH(y.nr, any64({&x, &y}),
-           return run_reduce(b, (OpCaxpyNorm<NR, T, false>{x, y, y, (T)ar, (T)ai}), nsites(y), out, 1, st));
+           return run_reduce(b, (OpCaxpyNorm<NR, T, false>{x, y, y, a}), nsites(y), out, 1, st, dres));
 }
-int blas_caxpy_norm_dot(Blas* b, double ar, double ai, const FieldRef& x, const FieldRef& y,
-                        const FieldRef& w, double out[3], cudaStream_t st) {
+int blas_caxpy_norm_dot(Blas* b, Cf a, const FieldRef& x, const FieldRef& y, const FieldRef& w,
+                        double out[3], cudaStream_t st, double* dres) {
   DISPATCH(y.nr, any64({&x, &y, &w}),
-           return run_reduce(b, (OpCaxpyNorm<NR, T, true>{x, y, w, (T)ar, (T)ai}), nsites(y), out, 3, st));
+           return run_reduce(b, (OpCaxpyNorm<NR, T, true>{x, y, w, a}), nsites(y), out, 3, st, dres));
 }
-int blas_scale_cdot(Blas* b, double s, const FieldRef& x, const FieldRef& y, double out[2],
-                    cudaStream_t st) {
+int blas_bicg_xr(Blas* b, Cf a, const FieldRef& p, Cf bb, const FieldRef& s, Cf c, const FieldRef& t,
+                 const FieldRef& xs, const FieldRef& w, double out[3], cudaStream_t st, double* dres) {
+  DISPATCH(s.nr, any64({&p, &s, &t, &xs, &w}),
+           return run_reduce(b, (OpBicgXR<NR, T>{p, s, t, xs, w, a, bb, c}), nsites(s), out, 3, st, dres));
+}
+int blas_cg_update(Blas* b, Cf a, const FieldRef& p, Cf c, const FieldRef& Ap, const FieldRef& xs,
+                   const FieldRef& r, double* out, cudaStream_t st, double* dres) {
+  DISPATCH(r.nr, any64({&p, &Ap, &xs, &r}),
+           return run_reduce(b, (OpCgUpdate<NR, T>{p, Ap, xs, r, a, c}), nsites(r), out, 1, st, dres));
+}
+int blas_scale_cdot(Blas* b, Cf s, const FieldRef& x, const FieldRef& y, double out[2], cudaStream_t st,
+                    double* dres) {
   DISPATCH(x.nr, any64({&x, &y}),
-           return run_reduce(b, (OpScaleCdot<NR, T>{x, y, (T)s}), nsites(x), out, 2, st));
+           return run_reduce(b, (OpScaleCdot<NR, T>{x, y, s}), nsites(x), out, 2, st, dres));
 }
-int blas_xmy_norm(Blas* b, const FieldRef& bb, const FieldRef& y, double* out, cudaStream_t st) {
+int blas_xmy_norm(Blas* b, const FieldRef& bb, const FieldRef& y, double* out, cudaStream_t st, double* dres) {
   DISPATCH(y.nr, any64({&bb, &y}),
-           return run_reduce(b, (OpXmyNorm<NR, T>{bb, y}), nsites(y), out, 1, st));
+           return run_reduce(b, (OpXmyNorm<NR, T>{bb, y}), nsites(y), out, 1, st, dres));
 }
-int blas_multi_caxpy(Blas* b, int n, const double* cr, const double* ci, const FieldRef* xs,
-                     const FieldRef& y, cudaStream_t st) {
+int blas_multishift_update(Blas* b, int n, const FieldRef* xs, const FieldRef* ps, const FieldRef& r,
+                           const double* coef, cudaStream_t st) {
+  if (n < 1 || n > kMaxMulti) {
+    b->err = "multi-shift update: 1..16 shifts";
+    return DIRAC_ERR_ARG;
+  }
+  ShiftFields f;
+  f.n = n;
+  bool dbl = r.prec == P64;
+  for (int j = 0; j < n; ++j) {
+    f.x[j] = xs[j];
+    f.p[j] = ps[j];
+    dbl = dbl || xs[j].prec == P64 || ps[j].prec == P64;
+  }
+  DISPATCH(r.nr, dbl, return run_map(b, (OpMultiShift<NR, T>{f, r, coef}), nsites(r), st));
+}
+
+int blas_multi_caxpy(Blas* b, int n, const Cf* c, const FieldRef* xs, const FieldRef& y, cudaStream_t st) {
   for (int j0 = 0; j0 < n; j0 += kMaxMulti) {
     MultiCoef m;
     m.n = n - j0 < kMaxMulti ? n - j0 : kMaxMulti;
     bool dbl = y.prec == P64;
     for (int j = 0; j < m.n; ++j) {
       m.x[j] = xs[j0 + j];
-      m.cr[j] = cr[j0 + j];
-      m.ci[j] = ci[j0 + j];
+      m.c[j] = c[j0 + j];
       dbl = dbl || xs[j0 + j].prec == P64;
     }
     int rc;

@@ -64,39 +64,58 @@ int launch_schwarz(int prec, int recon, char* out, const char* in, const char* g
                    double kappa, cudaStream_t st);
 
 // ---------------------------------------------------------------- BLAS (blas.cu)
+// A complex coefficient: the host value (r, i), or s * (p[0], p[1]) read on the device
+// when p is set (written there by an earlier reduction or a solver's scalar kernel).
+struct Cf {
+  double r = 0, i = 0;
+  const double* p = nullptr;
+  double s = 1;
+};
+inline Cf cval(double r, double i = 0) { Cf c; c.r = r; c.i = i; return c; }
+inline Cf cptr(const double* p, double s = 1) { Cf c; c.p = p; c.s = s; return c; }
+
 struct Blas;  // reduction scratch + pinned result slots
 Blas* blas_create();
 void blas_destroy(Blas*);
-// All scalars are host values; reductions synchronise the stream and return on host.
+// Reductions return their result on the host after a stream synchronisation, or, when
+// `dres` (3 doubles of device memory) is given, leave it there without synchronising.
 int blas_copy(Blas*, const FieldRef& dst, const FieldRef& src, cudaStream_t st);
 int blas_zero(Blas*, const FieldRef& x, cudaStream_t st);
-// y = a x + b y (complex a, b)
-int blas_axpby(Blas*, double ar, double ai, const FieldRef& x, double br, double bi,
-               const FieldRef& y, cudaStream_t st);
-// z = x + a y  (z may alias x or y)
-int blas_xpay_to(Blas*, const FieldRef& x, double ar, double ai, const FieldRef& y,
-                 const FieldRef& z, cudaStream_t st);
-// y += a x + b z
-int blas_axpbz_add(Blas*, double ar, double ai, const FieldRef& x, double br, double bi,
-                   const FieldRef& z, const FieldRef& y, cudaStream_t st);
-int blas_norm2(Blas*, const FieldRef& x, double* out, cudaStream_t st);
-int blas_cdot(Blas*, const FieldRef& x, const FieldRef& y, double out[2], cudaStream_t st);
+// y = a x + b y
+int blas_axpby(Blas*, Cf a, const FieldRef& x, Cf b, const FieldRef& y, cudaStream_t st);
+// p = r + b p + c v
+int blas_pupdate(Blas*, const FieldRef& r, Cf b, Cf c, const FieldRef& v, const FieldRef& p, cudaStream_t st);
+int blas_norm2(Blas*, const FieldRef& x, double* out, cudaStream_t st, double* dres = nullptr);
+int blas_cdot(Blas*, const FieldRef& x, const FieldRef& y, double out[2], cudaStream_t st,
+              double* dres = nullptr);
 // out = {Re (x,y), Im (x,y), ||x||^2}
-int blas_cdot_norm(Blas*, const FieldRef& x, const FieldRef& y, double out[3], cudaStream_t st);
+int blas_cdot_norm(Blas*, const FieldRef& x, const FieldRef& y, double out[3], cudaStream_t st,
+                   double* dres = nullptr);
 // y += a x; out = ||y||^2
-int blas_caxpy_norm(Blas*, double ar, double ai, const FieldRef& x, const FieldRef& y,
-                    double* out, cudaStream_t st);
+int blas_caxpy_norm(Blas*, Cf a, const FieldRef& x, const FieldRef& y, double* out, cudaStream_t st,
+                    double* dres = nullptr);
 // y += a x; out = {||y||^2, Re (w,y), Im (w,y)}
-int blas_caxpy_norm_dot(Blas*, double ar, double ai, const FieldRef& x, const FieldRef& y,
-                        const FieldRef& w, double out[3], cudaStream_t st);
-// x *= s (real); out = (x, y) after scaling
-int blas_scale_cdot(Blas*, double s, const FieldRef& x, const FieldRef& y, double out[2],
-                    cudaStream_t st);
+int blas_caxpy_norm_dot(Blas*, Cf a, const FieldRef& x, const FieldRef& y, const FieldRef& w,
+                        double out[3], cudaStream_t st, double* dres = nullptr);
+// xs += a p + b s; s += c t; out = {||s||^2, Re (w,s), Im (w,s)}
+int blas_bicg_xr(Blas*, Cf a, const FieldRef& p, Cf b, const FieldRef& s, Cf c, const FieldRef& t,
+                 const FieldRef& xs, const FieldRef& w, double out[3], cudaStream_t st,
+                 double* dres = nullptr);
+// xs += a p; r += c Ap; out = ||r||^2
+int blas_cg_update(Blas*, Cf a, const FieldRef& p, Cf c, const FieldRef& Ap, const FieldRef& xs,
+                   const FieldRef& r, double* out, cudaStream_t st, double* dres = nullptr);
+// x *= Re s; out = (x, y) after scaling
+int blas_scale_cdot(Blas*, Cf s, const FieldRef& x, const FieldRef& y, double out[2], cudaStream_t st,
+                    double* dres = nullptr);
 // y = b - y ; out = ||y||^2   (residual r = b - Ax with Ax held in y)
-int blas_xmy_norm(Blas*, const FieldRef& b, const FieldRef& y, double* out, cudaStream_t st);
-// y += sum_i c_i x_i (n <= 32 vectors of one precision), complex coefficients
-int blas_multi_caxpy(Blas*, int n, const double* c_re, const double* c_im, const FieldRef* xs,
-                     const FieldRef& y, cudaStream_t st);
+int blas_xmy_norm(Blas*, const FieldRef& b, const FieldRef& y, double* out, cudaStream_t st,
+                  double* dres = nullptr);
+// y += sum_i c_i x_i
+int blas_multi_caxpy(Blas*, int n, const Cf* c, const FieldRef* xs, const FieldRef& y, cudaStream_t st);
+// multi-shift CG: x_j += a_j p_j; p_j = z_j r + b_j p_j for the active j (coef on device,
+// 4 doubles per shift: a, z, b, active), n <= 16
+int blas_multishift_update(Blas*, int n, const FieldRef* xs, const FieldRef* ps, const FieldRef& r,
+                           const double* coef, cudaStream_t st);
 const char* blas_error(Blas*);
 
 // ---------------------------------------------------------------- api.cu helpers
@@ -105,8 +124,9 @@ int cuda_check(dirac_ctx* c, const char* what);
 FieldRef field_ref(const dirac_ctx* c, const void* p, int prec, int parity);
 int check_op(dirac_ctx* c, int prec, bool need_schwarz);
 int ensure_tmp(dirac_ctx* c, int prec);
-// which: 0 = M, 1 = M^dagger, 2 = M^dagger M; parity FULL(-1) / EVEN / ODD
-int apply_op(dirac_ctx* c, char* out, const char* in, int parity, int prec, int which, cudaStream_t st);
+// which: 0 = M, 1 = M^dagger, 2 = M^dagger M (+ shift); parity FULL(-1) / EVEN / ODD
+int apply_op(dirac_ctx* c, char* out, const char* in, int parity, int prec, int which, cudaStream_t st,
+             double shift = 0.0);
 int schwarz_apply(dirac_ctx* c, char* out, const char* in, int prec, cudaStream_t st);
 
 }  // namespace dirac
@@ -130,6 +150,10 @@ struct dirac_ctx {
   // solver work fields (solvers.cu), grown on demand and kept until destroy
   char* work[48] = {};
   size_t work_bytes[48] = {};
+  // solver scalars: device slots, a mapped host mirror of per-iteration residuals
+  double* dscal = nullptr;
+  double* hmirror = nullptr;
+  double* dmirror = nullptr;
   // device staging for natural-layout spinors passed from host memory
   char* staging = nullptr;
   size_t staging_bytes = 0;

@@ -76,6 +76,8 @@ _SIGS = {
     "solve": (_ci, [_vp, _vp, _vp, ctypes.POINTER(SolverParams), ctypes.POINTER(SolverStats), _vp]),
     "dirac_cdot_noalloc": (_ci, [_vp, _vp, _ci, _ci, ctypes.c_longlong, _ci, _vp, _vp,
                                  ctypes.c_char_p, _sz]),
+    "solve_multishift": (_ci, [_vp, ctypes.POINTER(_vp), _vp, ctypes.POINTER(ctypes.c_double), _ci,
+                               ctypes.POINTER(SolverParams), ctypes.POINTER(SolverStats), _vp]),
 }
 EXPORTED = tuple(_SIGS)
 for _name, (_res, _args) in _SIGS.items():
@@ -246,3 +248,19 @@ class Lattice:
         d = st.as_dict()
         d["status"] = ERR_NAMES.get(rc, rc)
         return d
+
+    def solve_multishift(self, xs, b, shifts, alg, tol=1e-10, max_iter=10000, delta=0.1,
+                         prec_sloppy=F32, stream=None, raise_on_error=True):
+        """Eq. 4: (M^dagger M + sigma_j) x_j = b for every shift (Sec. 8.2 strategy).
+        Returns the stats of the multi-shift stage and of each refinement."""
+        n = len(shifts)
+        sp = SolverParams(alg, tol, max_iter, 16, delta, 1, prec_sloppy, prec_sloppy)
+        st = (SolverStats * (n + 1))()
+        ptrs = (_vp * n)(*[x.data_ptr() for x in xs])
+        sh = (ctypes.c_double * n)(*shifts)
+        rc = solve_multishift(self.ctx, ptrs, b.data_ptr(), sh, n, ctypes.byref(sp), st,
+                              _stream(stream))
+        if raise_on_error and rc != OK:
+            raise DiracError(rc, f"solve_multishift: {dirac_last_error(self.ctx).decode()}")
+        return {"status": ERR_NAMES.get(rc, rc), "multishift": st[0].as_dict(),
+                "refine": [st[1 + j].as_dict() for j in range(n)]}

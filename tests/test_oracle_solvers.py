@@ -160,3 +160,38 @@ def test_staggered_even_cg_matches_dense():
     idx = np.repeat(np.where(even.ravel())[0] * 3, 3) + np.tile(np.arange(3), even.sum())
     xe = np.linalg.solve(Dn[np.ix_(idx, idx)], b.ravel()[idx])
     assert np.linalg.norm(x.ravel()[idx] - xe) / np.linalg.norm(xe) < 1e-10
+
+
+def test_multishift_cg_matches_dense_for_every_shift():
+    """Eq. 4: (M^dagger M + sigma_i) x_i = b, all shifts in one Krylov space, each
+    solution equal to a dense solve, all done in the iterations of the smallest shift."""
+    dims = (4, 4, 4, 4)
+    fat, lng = synth.asqtad_links(dims, 51, 52)
+    fat, lng = fat.numpy(), lng.numpy()
+    m = 0.05
+    even = staggered.parity_mask(dims, 0)
+    N = lambda v: staggered.apply_normal(fat, lng, m, v) * even[..., None]
+    b = synth.staggered_spinor(dims, 53, parity=0).numpy()
+    shifts = [0.3, 0.0, 0.02, 1.5]
+    xs, info = solvers.multishift_cg(N, b, shifts, 1e-12, 2000)
+    Dn = _dense(N, b.shape)
+    idx = np.repeat(np.where(even.ravel())[0] * 3, 3) + np.tile(np.arange(3), even.sum())
+    Ae = Dn[np.ix_(idx, idx)]
+    for sgm, x in zip(shifts, xs):
+        xe = np.linalg.solve(Ae + sgm * np.eye(len(idx)), b.ravel()[idx])
+        assert np.linalg.norm(x.ravel()[idx] - xe) / np.linalg.norm(xe) < 1e-10, sgm
+    # the base (smallest-shift) system alone takes as many iterations
+    _, info0 = solvers.cg(N, b, 1e-12, 2000)
+    assert info["iters"] == info0["iters"]
+
+
+def test_multishift_single_shift_is_plain_cg():
+    dims = (2, 2, 2, 4)
+    U = synth.wilson_gauge(dims, 0.5, 1, 61).numpy()
+    A = wilson.clover(U, 1.0)
+    Md = lambda v: wilson.apply_M(U, A, 0.12, v, dagger=True)
+    N = lambda v: Md(wilson.apply_M(U, A, 0.12, v)) + 0.1 * v
+    b = synth.wilson_spinor(dims, 62).numpy()
+    (x,), _ = solvers.multishift_cg(lambda v: Md(wilson.apply_M(U, A, 0.12, v)), b, [0.1], 1e-12, 500)
+    x0, _ = solvers.cg(N, b, 1e-12, 500)
+    assert np.linalg.norm(x - x0) / np.linalg.norm(x0) < 1e-12
