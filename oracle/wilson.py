@@ -172,3 +172,63 @@ def apply_M_sites(U, csw, kappa, psi, sites, antiperiodic_t=True, dagger=False, 
     v = at(psi, xs).reshape(len(xs), 12)
     out = np.einsum("nij,nj->ni", Ahat, v).reshape(len(xs), 4, 3)
     return out - kappa * dslash(U, psi, antiperiodic_t, xs, dagger=dagger)
+
+
+# ---------------------------------------------------------------------------
+# Even-odd (Schur complement) form of the Wilson-clover operator (Sec. 3.1)
+# ---------------------------------------------------------------------------
+
+def clover_hat_inverse(A, kappa):
+    """(1 + 2 kappa A)^-1 per site; A natural (T,Z,Y,X,12,12) or None (identity)."""
+    if A is None:
+        return None
+    Ahat = np.eye(12) + 2.0 * kappa * A
+    return np.linalg.inv(Ahat)
+
+
+def _apply_site_matrix(Mx, psi):
+    """psi(x) -> Mx(x) psi(x) for natural arrays (Mx None = identity)."""
+    if Mx is None:
+        return psi.copy()
+    sh = psi.shape
+    return np.einsum("...ij,...j->...i", Mx, psi.reshape(sh[:4] + (12,))).reshape(sh)
+
+
+def _clover_hat(A, kappa, psi):
+    return psi if A is None else psi + 2.0 * kappa * apply_clover(A, psi)
+
+
+def parity_mask(dims, parity):
+    LX, LY, LZ, LT = dims
+    t, z, y, x = np.meshgrid(np.arange(LT), np.arange(LZ), np.arange(LY), np.arange(LX), indexing="ij")
+    return ((x + y + z + t) % 2 == parity)[..., None, None]
+
+
+def apply_schur(U, A, kappa, psi_e, antiperiodic_t=True, dagger=False):
+    """Even-site Schur complement of M_kappa = [[Ahat_ee, -kappa D_eo], [-kappa D_oe, Ahat_oo]]:
+        Mhat psi_e = Ahat_ee psi_e - kappa^2 D_eo Ahat_oo^-1 D_oe psi_e
+    (adjoint: D replaced by D^dagger; Ahat is Hermitian). ``psi_e`` is a natural array
+    whose odd sites are ignored; the result is zero on odd sites."""
+    dims = dims_of(psi_e)
+    ev, od = parity_mask(dims, 0), parity_mask(dims, 1)
+    inv = clover_hat_inverse(A, kappa)
+    t = dslash(U, psi_e * ev, antiperiodic_t, dagger=dagger) * od
+    t = _apply_site_matrix(inv, t) * od
+    u = dslash(U, t, antiperiodic_t, dagger=dagger) * ev
+    return (_clover_hat(A, kappa, psi_e * ev) - kappa * kappa * u) * ev
+
+
+def schur_source(U, A, kappa, b, antiperiodic_t=True):
+    """bhat_e = b_e + kappa D_eo Ahat_oo^-1 b_o (zero on odd sites)."""
+    dims = dims_of(b)
+    ev, od = parity_mask(dims, 0), parity_mask(dims, 1)
+    t = _apply_site_matrix(clover_hat_inverse(A, kappa), b * od) * od
+    return (b + kappa * dslash(U, t, antiperiodic_t)) * ev
+
+
+def schur_reconstruct(U, A, kappa, b, x_e, antiperiodic_t=True):
+    """Full solution from the even one: x_o = Ahat_oo^-1 (b_o + kappa D_oe x_e)."""
+    dims = dims_of(b)
+    ev, od = parity_mask(dims, 0), parity_mask(dims, 1)
+    u = (b + kappa * dslash(U, x_e * ev, antiperiodic_t)) * od
+    return x_e * ev + _apply_site_matrix(clover_hat_inverse(A, kappa), u) * od
