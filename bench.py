@@ -567,7 +567,9 @@ def run_solves(dirac, synth, U, src, dev):
         runs = [("gcr_dd_mixed", dirac.GCR_DD, dirac.F16, dirac.F16, 0.1),
                 ("gcr_dd_f64", dirac.GCR_DD, dirac.F64, dirac.F64, 0.0),
                 ("bicgstab_mixed", dirac.BICGSTAB, dirac.F16, dirac.F16, 0.1),
-                ("bicgstab_f64", dirac.BICGSTAB, dirac.F64, dirac.F64, 0.0)]
+                ("bicgstab_f64", dirac.BICGSTAB, dirac.F64, dirac.F64, 0.0),
+                ("bicgstab_eo_mixed", dirac.BICGSTAB_EO, dirac.F16, dirac.F16, 0.1),
+                ("bicgstab_eo_f64", dirac.BICGSTAB_EO, dirac.F64, dirac.F64, 0.0)]
         for name, alg, sp, pp, delta in runs:
             if kappa == KAPPA and name.endswith("f64"):
                 continue
@@ -575,7 +577,7 @@ def run_solves(dirac, synth, U, src, dev):
             st = lat.solve(x, b, alg, tol=1e-10, max_iter=budget if alg != dirac.GCR_DD else budget // 4,
                            k_max=16, delta=delta, prec_sloppy=sp, prec_precond=pp, raise_on_error=False)
             res[name] = {k: (float(f"{v:.4g}") if isinstance(v, float) else v) for k, v in st.items()}
-        for alg in ("gcr_dd", "bicgstab"):
+        for alg in ("gcr_dd", "bicgstab", "bicgstab_eo"):
             a, b_ = res.get(f"{alg}_mixed"), res.get(f"{alg}_f64")
             if a and b_ and a["status"] == "OK" and b_["status"] == "OK":
                 res[f"{alg}_speedup_vs_f64"] = round(b_["seconds"] / a["seconds"], 3)

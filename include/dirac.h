@@ -122,6 +122,12 @@ int dirac_apply_dagger(dirac_ctx* ctx, void* out, const void* in, dirac_parity p
 int dirac_apply_normal(dirac_ctx* ctx, void* out, const void* in, dirac_parity parity,
                        dirac_prec prec, void* stream);
 
+/* Even-odd (Schur complement) form of the Wilson-clover operator (Sec. 3.1: even-odd
+ * preconditioning, solving the Schur complement system): on EVEN half-fields
+ *     out = Ahat_ee in - kappa^2 D_eo Ahat_oo^-1 D_oe in      (dagger = 1: the adjoint)
+ * with Ahat^-1 built alongside Ahat by dirac_load_gauge. Wilson-clover only. */
+int dirac_apply_eo(dirac_ctx* ctx, void* out, const void* in, dirac_prec prec, int dagger, void* stream);
+
 /* out = K in: the non-overlapping additive Schwarz preconditioner of Sec. 3.2 / 8.1
  * for the Wilson-clover operator. On every block (params.block) the operator with
  * Dirichlet (zero) block boundaries is solved by params.mr_steps minimal-residual
@@ -172,7 +178,10 @@ typedef enum {
   DIRAC_SOLVER_CG_EVEN_NORMAL = 1, /* CG on (M^dagger M)_ee x_e = b_e, asqtad (Sec. 3.1) */
   DIRAC_SOLVER_BICGSTAB = 2,       /* BiCGstab on M x = b, Wilson-clover (Sec. 3.1) */
   DIRAC_SOLVER_GCR_DD = 3,         /* GCR with the Schwarz preconditioner (Algorithm 1) */
-  DIRAC_SOLVER_GCR = 4             /* GCR of Algorithm 1 with K = 1 */
+  DIRAC_SOLVER_GCR = 4,            /* GCR of Algorithm 1 with K = 1 */
+  DIRAC_SOLVER_BICGSTAB_EO = 5,    /* BiCGstab on the even-odd Schur system (Sec. 3.1), then
+                                      x_o = Ahat_oo^-1 (b_o + kappa D_oe x_e); x, b full fields */
+  DIRAC_SOLVER_GCR_EO = 6          /* unpreconditioned GCR on the even-odd Schur system */
 } dirac_solver;
 
 typedef struct {

@@ -86,8 +86,10 @@ int wilson_M(dirac_ctx* c, char* out, const char* in, int prec, bool dag, cudaSt
   return cuda_check(c, "wilson M kernel");
 }
 
-// Wilson: out_p = D_{p,1-p} in_{1-p} (half-fields).
-int wilson_hop(dirac_ctx* c, char* out, const char* in, int parity, int prec, bool dag, cudaStream_t st) {
+// Wilson, half-fields: out_p = Cpost (Cself self_p + s D_{p,1-p} in_{1-p}) (defaults:
+// the plain hopping block out_p = D_{p,1-p} in_{1-p}).
+int wilson_hop(dirac_ctx* c, char* out, const char* in, int parity, int prec, bool dag, cudaStream_t st,
+               double s, const char* self, const char* c_self, const char* c_post) {
   WilsonArg a;
   a.out[0] = a.out[1] = out;
   a.in[0] = a.in[1] = in;
@@ -97,8 +99,43 @@ int wilson_hop(dirac_ctx* c, char* out, const char* in, int parity, int prec, bo
   a.kappa = c->p.kappa;
   a.dagger = dag;
   a.out_parity = parity;
+  a.s = s;
+  a.self = self;
+  a.c_self = c_self;
+  a.c_post = c_post;
   wilson_launch(prec, c->p.recon[prec], false, a, st);
   return cuda_check(c, "wilson dslash kernel");
+}
+
+// clover-format matrices for parity p (null = identity when c_sw = 0)
+static const char* clov(dirac_ctx* c, int prec) { return c->p.csw != 0.0 ? c->clover[prec] : nullptr; }
+static const char* clov_inv(dirac_ctx* c, int prec) { return c->p.csw != 0.0 ? c->clover_inv[prec] : nullptr; }
+
+// Even-odd (Schur complement) operator on even half-fields (Sec. 3.1):
+//   Mhat in_e = Ahat_ee in_e - kappa^2 D_eo Ahat_oo^-1 D_oe in_e
+int schur_apply(dirac_ctx* c, char* out, const char* in, int prec, bool dag, cudaStream_t st) {
+  int rc;
+  if ((rc = ensure_tmp(c, prec))) return rc;
+  char* t = c->tmp[prec];  // odd half-field
+  if ((rc = wilson_hop(c, t, in, 1, prec, dag, st, 1.0, nullptr, nullptr, clov_inv(c, prec)))) return rc;
+  const double k2 = c->p.kappa * c->p.kappa;
+  return wilson_hop(c, out, t, 0, prec, dag, st, -k2, in, clov(c, prec), nullptr);
+}
+
+// bhat_e = b_e + kappa D_eo Ahat_oo^-1 b_o   (b full field; bhat even half-field)
+int schur_source(dirac_ctx* c, char* bhat, const char* b, int prec, cudaStream_t st) {
+  int rc;
+  if ((rc = ensure_tmp(c, prec))) return rc;
+  const size_t hb = spinor_half_bytes(prec, 24, c->Vh);
+  char* t = c->tmp[prec];
+  if ((rc = wilson_hop(c, t, b, 1, prec, false, st, 0.0, b + hb, clov_inv(c, prec), nullptr))) return rc;
+  return wilson_hop(c, bhat, t, 0, prec, false, st, c->p.kappa, b, nullptr, nullptr);
+}
+
+// x_o = Ahat_oo^-1 (b_o + kappa D_oe x_e)   (x full field whose even half is solved)
+int schur_reconstruct(dirac_ctx* c, char* x, const char* b, int prec, cudaStream_t st) {
+  const size_t hb = spinor_half_bytes(prec, 24, c->Vh);
+  return wilson_hop(c, x + hb, x, 1, prec, false, st, c->p.kappa, b + hb, nullptr, clov_inv(c, prec));
 }
 
 // Asqtad: out_p = a x_p + b D_{p,1-p} in_{1-p}
@@ -137,10 +174,14 @@ int apply_op(dirac_ctx* c, char* out, const char* in, int parity, int prec, int 
       if ((rc = stag_hop(c, out + p * hb, t + (1 - p) * hb, in + p * hb, p, prec, m2, -0.25, st))) return rc;
     return DIRAC_OK;
   }
+  if (which == 3 || which == 4) {  // even-odd Schur operator (4: adjoint), even half-fields
+    if (!wil || parity != 0) return set_err(c, DIRAC_ERR_UNSUPPORTED, "Schur operator: Wilson-clover, even sites");
+    return schur_apply(c, out, in, prec, which == 4, st);
+  }
   const bool dag = which == 1;
   if (wil) {
     if (parity < 0) return wilson_M(c, out, in, prec, dag, st);
-    return wilson_hop(c, out, in, parity, prec, dag, st);
+    return wilson_hop(c, out, in, parity, prec, dag, st, 1.0, nullptr, nullptr, nullptr);
   }
   if (parity >= 0) return stag_hop(c, out, in, nullptr, parity, prec, 0.0, dag ? -1.0 : 1.0, st);
   for (int p = 0; p < 2; ++p)  // M = m - D/2, M^dagger = m + D/2
@@ -216,7 +257,7 @@ int dirac_destroy(dirac_ctx* c) {
   bool ok = true;
   auto fr = [&](void* p) { if (p && cudaFree(p) != cudaSuccess) ok = false; };
   for (int q = 0; q < 3; ++q)
-    for (char* p : {c->gauge[q], c->fat[q], c->clover[q], c->tmp[q], c->tmp2[q]}) fr(p);
+    for (char* p : {c->gauge[q], c->fat[q], c->clover[q], c->clover_inv[q], c->tmp[q], c->tmp2[q]}) fr(p);
   for (int i = 0; i < 48; ++i) fr(c->work[i]);
   fr(c->staging);
   fr(c->dscal);
@@ -258,10 +299,14 @@ int dirac_load_gauge(dirac_ctx* c, const double* links, int which, int on_device
     if ((rc = cuda_check(c, "pack links"))) break;
   }
   if (!rc && which == 0) {
+    const bool inv = c->p.csw != 0.0;
     for (int q = 0; q < 3 && !rc; ++q)
-      if (c->mask & (1u << q)) rc = dalloc(c, &c->clover[q], 2 * clover_parity_bytes(q, c->Vh));
+      if (c->mask & (1u << q)) {
+        rc = dalloc(c, &c->clover[q], 2 * clover_parity_bytes(q, c->Vh));
+        if (!rc && inv) rc = dalloc(c, &c->clover_inv[q], 2 * clover_parity_bytes(q, c->Vh));
+      }
     if (!rc) {
-      launch_build_clover(src, c->g, c->p.kappa, c->p.csw, c->clover, c->mask, st);
+      launch_build_clover(src, c->g, c->p.kappa, c->p.csw, c->clover, inv ? c->clover_inv : nullptr, c->mask, st);
       rc = cuda_check(c, "build clover");
     }
   }
@@ -338,6 +383,15 @@ int dirac_apply_dagger(dirac_ctx* c, void* out, const void* in, dirac_parity par
 int dirac_apply_normal(dirac_ctx* c, void* out, const void* in, dirac_parity parity, dirac_prec prec,
                        void* stream) {
   return apply_entry(c, out, in, parity, prec, 2, stream);
+}
+
+int dirac_apply_eo(dirac_ctx* c, void* out, const void* in, dirac_prec prec, int dagger, void* stream) {
+  int rc = check_op(c, prec, false);
+  if (rc) return rc;
+  if (c->p.kind != DIRAC_WILSON_CLOVER)
+    return set_err(c, DIRAC_ERR_UNSUPPORTED, "the even-odd operator is defined for Wilson-clover");
+  if (!out || !in || out == in) return set_err(c, DIRAC_ERR_ARG, "null or aliased fields");
+  return apply_op(c, (char*)out, (const char*)in, 0, prec, dagger ? 4 : 3, (cudaStream_t)stream);
 }
 
 int schwarz_precondition(dirac_ctx* c, void* out, const void* in, dirac_prec prec, void* stream) {

@@ -81,9 +81,59 @@ __device__ __forceinline__ M2 dag2(const M2& a) {
   return c;
 }
 
+// Inverse of a 6x6 complex matrix by Gauss-Jordan elimination with partial pivoting.
+// Returns false for a singular matrix.
+__device__ bool invert6(cd M[6][6], cd Inv[6][6]) {
+  for (int r = 0; r < 6; ++r)
+    for (int c = 0; c < 6; ++c) Inv[r][c] = cd{r == c ? 1.0 : 0.0, 0.0};
+  for (int col = 0; col < 6; ++col) {
+    int piv = col;
+    double best = M[col][col].r * M[col][col].r + M[col][col].i * M[col][col].i;
+    for (int r = col + 1; r < 6; ++r) {
+      double m = M[r][col].r * M[r][col].r + M[r][col].i * M[r][col].i;
+      if (m > best) { best = m; piv = r; }
+    }
+    if (!(best > 0)) return false;
+    if (piv != col)
+      for (int c = 0; c < 6; ++c) {
+        cd t = M[col][c]; M[col][c] = M[piv][c]; M[piv][c] = t;
+        t = Inv[col][c]; Inv[col][c] = Inv[piv][c]; Inv[piv][c] = t;
+      }
+    // 1 / pivot
+    const cd p = M[col][col];
+    const double d = p.r * p.r + p.i * p.i;
+    const cd ip = {p.r / d, -p.i / d};
+    for (int c = 0; c < 6; ++c) {
+      M[col][c] = ip * M[col][c];
+      Inv[col][c] = ip * Inv[col][c];
+    }
+    for (int r = 0; r < 6; ++r) {
+      if (r == col) continue;
+      const cd f = M[r][col];
+      for (int c = 0; c < 6; ++c) {
+        M[r][c] = M[r][c] - f * M[col][c];
+        Inv[r][c] = Inv[r][c] - f * Inv[col][c];
+      }
+    }
+  }
+  return true;
+}
+
+// pack a Hermitian 6x6 block: 6 real diagonal entries, then the 15 entries below the
+// diagonal (row-major), symmetrised (the average of H_rc and conj(H_cr))
+__device__ void pack_herm6(const cd H[6][6], double* o) {
+  for (int r = 0; r < 6; ++r) o[r] = H[r][r].r;
+  int k = 6;
+  for (int r = 1; r < 6; ++r)
+    for (int c = 0; c < r; ++c) {
+      o[k++] = 0.5 * (H[r][c].r + H[c][r].r);
+      o[k++] = 0.5 * (H[r][c].i - H[c][r].i);
+    }
+}
+
 template <int NP>
 __global__ void build_clover_kernel(const double* links, Geom g, double kappa, double csw,
-                                    char* d64, char* d32, char* d16) {
+                                    char* d64, char* d32, char* d16, char* i64, char* i32, char* i16) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= 2 * (int64_t)g.Vh) return;
   int par = (int)(i / g.Vh), cb = (int)(i - (int64_t)par * g.Vh);
@@ -142,29 +192,32 @@ __global__ void build_clover_kernel(const double* links, Geom g, double kappa, d
           }
     }
   double v[72];
-  for (int b = 0; b < 2; ++b) {
-    double* o = v + 36 * b;
-    for (int r = 0; r < 6; ++r) o[r] = A[b][r][r].r;
-    int k = 6;
-    for (int r = 1; r < 6; ++r)
-      for (int c = 0; c < r; ++c) {
-        o[k++] = A[b][r][c].r;
-        o[k++] = A[b][r][c].i;
-      }
-  }
+  for (int b = 0; b < 2; ++b) pack_herm6(A[b], v + 36 * b);
   if (d64) CloverIO<P64>::store(d64 + (size_t)par * CloverIO<P64>::parity_bytes(g.Vh), g.Vh, cb, v);
   if (d32) CloverIO<P32>::store(d32 + (size_t)par * CloverIO<P32>::parity_bytes(g.Vh), g.Vh, cb, v);
   if (d16) CloverIO<P16>::store(d16 + (size_t)par * CloverIO<P16>::parity_bytes(g.Vh), g.Vh, cb, v);
+  if (i64 || i32 || i16) {
+    // Ahat^-1 for the even-odd (Schur complement) operator; NaN marks a singular block
+    for (int b = 0; b < 2; ++b) {
+      cd Inv[6][6];
+      if (!invert6(A[b], Inv))
+        for (int r = 0; r < 6; ++r)
+          for (int c = 0; c < 6; ++c) Inv[r][c] = cd{nan(""), nan("")};
+      pack_herm6(Inv, v + 36 * b);
+    }
+    if (i64) CloverIO<P64>::store(i64 + (size_t)par * CloverIO<P64>::parity_bytes(g.Vh), g.Vh, cb, v);
+    if (i32) CloverIO<P32>::store(i32 + (size_t)par * CloverIO<P32>::parity_bytes(g.Vh), g.Vh, cb, v);
+    if (i16) CloverIO<P16>::store(i16 + (size_t)par * CloverIO<P16>::parity_bytes(g.Vh), g.Vh, cb, v);
+  }
 }
 
 void launch_build_clover(const double* links, const Geom& g, double kappa, double csw,
-                         char* const dst[3], unsigned prec_mask, cudaStream_t st) {
+                         char* const dst[3], char* const inv[3], unsigned prec_mask, cudaStream_t st) {
   int64_t n = 2 * (int64_t)g.Vh;
   dim3 grid((unsigned)((n + 127) / 128)), block(128);
-  build_clover_kernel<0><<<grid, block, 0, st>>>(links, g, kappa, csw,
-                                                 (prec_mask & 1) ? dst[0] : nullptr,
-                                                 (prec_mask & 2) ? dst[1] : nullptr,
-                                                 (prec_mask & 4) ? dst[2] : nullptr);
+  auto pick = [&](char* const* a, int q) { return (a && (prec_mask & (1u << q))) ? a[q] : nullptr; };
+  build_clover_kernel<0><<<grid, block, 0, st>>>(links, g, kappa, csw, pick(dst, 0), pick(dst, 1),
+                                                 pick(dst, 2), pick(inv, 0), pick(inv, 1), pick(inv, 2));
 }
 
 }  // namespace dirac

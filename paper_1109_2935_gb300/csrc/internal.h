@@ -55,8 +55,9 @@ void launch_export_spinor(int prec, int nr, double* dst, int parity, const char*
                           cudaStream_t st);
 void launch_pack_links(int prec, int recon, char* dst, const double* src, const Geom& g,
                        cudaStream_t st);
+// Ahat = 1 + 2 kappa A into dst[p]; Ahat^-1 into inv[p] when inv is not null
 void launch_build_clover(const double* links, const Geom& g, double kappa, double csw,
-                         char* const dst[3], unsigned prec_mask, cudaStream_t st);
+                         char* const dst[3], char* const inv[3], unsigned prec_mask, cudaStream_t st);
 
 // Schwarz block-MR preconditioner
 int launch_schwarz(int prec, int recon, char* out, const char* in, const char* gauge,
@@ -124,10 +125,16 @@ int cuda_check(dirac_ctx* c, const char* what);
 FieldRef field_ref(const dirac_ctx* c, const void* p, int prec, int parity);
 int check_op(dirac_ctx* c, int prec, bool need_schwarz);
 int ensure_tmp(dirac_ctx* c, int prec);
-// which: 0 = M, 1 = M^dagger, 2 = M^dagger M (+ shift); parity FULL(-1) / EVEN / ODD
+// which: 0 = M, 1 = M^dagger, 2 = M^dagger M (+ shift), 3 / 4 = even-odd Schur operator /
+// its adjoint (Wilson-clover, parity EVEN); parity FULL(-1) / EVEN / ODD
 int apply_op(dirac_ctx* c, char* out, const char* in, int parity, int prec, int which, cudaStream_t st,
              double shift = 0.0);
 int schwarz_apply(dirac_ctx* c, char* out, const char* in, int prec, cudaStream_t st);
+// even-odd form (Wilson-clover): bhat_e = b_e + kappa D_eo Ahat_oo^-1 b_o and
+// x_o = Ahat_oo^-1 (b_o + kappa D_oe x_e); which = 3 / 4 in apply_op is the Schur
+// operator / its adjoint on even half-fields
+int schur_source(dirac_ctx* c, char* bhat, const char* b, int prec, cudaStream_t st);
+int schur_reconstruct(dirac_ctx* c, char* x, const char* b, int prec, cudaStream_t st);
 
 }  // namespace dirac
 
@@ -142,6 +149,7 @@ struct dirac_ctx {
   char* gauge[3] = {nullptr, nullptr, nullptr};   // Wilson U or asqtad long links
   char* fat[3] = {nullptr, nullptr, nullptr};     // asqtad fat links
   char* clover[3] = {nullptr, nullptr, nullptr};  // Wilson-clover Ahat
+  char* clover_inv[3] = {nullptr, nullptr, nullptr};  // Ahat^-1 (c_sw != 0)
   bool have_gauge = false, have_fat = false, have_long = false;
   // scratch spinors for composite operators, per precision (full fields)
   char* tmp[3] = {nullptr, nullptr, nullptr};

@@ -662,6 +662,8 @@ int ensure_scalars(dirac_ctx* c) {
 // operator flops per application (Wilson-clover 1872/site, plain Wilson 1368/site,
 // asqtad hopping term 1146/output site plus the diagonal)
 double op_flops(const dirac_ctx* c, int which, int parity) {
+  if (c->p.kind == DIRAC_WILSON_CLOVER && which >= 3)  // Schur: 2 hops + Ahat + Ahat^-1
+    return (double)c->Vh * (2 * 1320.0 + (c->p.csw != 0 ? 2 * 504.0 : 0.0) + 48.0);
   if (c->p.kind == DIRAC_WILSON_CLOVER)
     return (double)c->V * (c->p.csw != 0 ? 1872.0 : 1368.0) * (which == 2 ? 2 : 1);
   return which == 2 ? (parity >= 0 ? 2.0 * 1146.0 * c->Vh + 12.0 * c->Vh : 2.0 * 1158.0 * c->V)
@@ -757,7 +759,12 @@ extern "C" int solve(dirac_ctx* c, void* x, const void* b, const dirac_solver_pa
   const dirac_solver_params& P = *params;
   const bool wil = c->p.kind == DIRAC_WILSON_CLOVER;
   int parity = -1, which = 0;
+  bool eo = false;
   switch (P.alg) {
+    case DIRAC_SOLVER_BICGSTAB_EO:
+    case DIRAC_SOLVER_GCR_EO:
+      if (!wil) return set_err(c, DIRAC_ERR_UNSUPPORTED, "even-odd solvers need the Wilson-clover operator");
+      which = 3; parity = 0; eo = true; break;
     case DIRAC_SOLVER_CG_NORMAL: which = 2; break;
     case DIRAC_SOLVER_CG_EVEN_NORMAL:
       if (wil) return set_err(c, DIRAC_ERR_UNSUPPORTED, "CG_EVEN_NORMAL needs the asqtad operator");
@@ -788,12 +795,29 @@ extern "C" int solve(dirac_ctx* c, void* x, const void* b, const dirac_solver_pa
       return set_err(c, DIRAC_ERR_CUDA, "cudaEventCreate");
   S.flops_per_apply = op_flops(c, which, parity);
   auto t0 = std::chrono::steady_clock::now();
-  switch (P.alg) {
-    case DIRAC_SOLVER_CG_NORMAL:
-    case DIRAC_SOLVER_CG_EVEN_NORMAL: rc = solve_cg(S, (char*)x, (const char*)b, P); break;
-    case DIRAC_SOLVER_BICGSTAB: rc = solve_bicgstab(S, (char*)x, (const char*)b, P); break;
-    case DIRAC_SOLVER_GCR_DD: rc = solve_gcr(S, (char*)x, (const char*)b, P, true); break;
-    default: rc = solve_gcr(S, (char*)x, (const char*)b, P, false); break;
+  if (eo) {
+    // Sec. 3.1: solve the Schur complement system on the even sites, then rebuild x_o.
+    // The even half of the caller's full field x is the even half-field solved for.
+    char* bhat = S.get(P64);
+    if (!bhat) rc = set_err(c, DIRAC_ERR_OOM, "solver workspace");
+    else rc = schur_source(c, bhat, (const char*)b, P64, s);
+    if (rc == DIRAC_OK) {
+      if (P.alg == DIRAC_SOLVER_BICGSTAB_EO) rc = solve_bicgstab(S, (char*)x, bhat, P);
+      else rc = solve_gcr(S, (char*)x, bhat, P, false);
+    }
+    if (rc == DIRAC_OK) rc = schur_reconstruct(c, (char*)x, (const char*)b, P64, s);
+    // the final check is on the full system M x = b
+    S.which = 0;
+    S.parity = -1;
+    S.flops_per_apply = op_flops(c, 0, -1);
+  } else {
+    switch (P.alg) {
+      case DIRAC_SOLVER_CG_NORMAL:
+      case DIRAC_SOLVER_CG_EVEN_NORMAL: rc = solve_cg(S, (char*)x, (const char*)b, P); break;
+      case DIRAC_SOLVER_BICGSTAB: rc = solve_bicgstab(S, (char*)x, (const char*)b, P); break;
+      case DIRAC_SOLVER_GCR_DD: rc = solve_gcr(S, (char*)x, (const char*)b, P, true); break;
+      default: rc = solve_gcr(S, (char*)x, (const char*)b, P, false); break;
+    }
   }
   if (rc == DIRAC_OK) rc = finish_stats(S, (const char*)x, (const char*)b, P.tol);
   cudaError_t e = cudaStreamSynchronize(s);

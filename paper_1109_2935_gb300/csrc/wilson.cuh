@@ -25,6 +25,13 @@ struct WilsonArg {
   double kappa;
   int dagger;            // 1: apply the adjoint
   int out_parity;        // hop mode: parity of the output half-field
+  // hop mode: out_p = Cpost (Cself self_p + s D_{p,1-p} in_{1-p}); a null matrix is the
+  // identity, a null self drops that term, s = 0 skips the hopping term. Cself / Cpost
+  // are clover-format fields ([parity][chunk][Vh]: Ahat or Ahat^-1).
+  const char* self = nullptr;
+  const char* c_self = nullptr;
+  const char* c_post = nullptr;
+  double s = 1.0;
 };
 
 template <int MU, typename T>
@@ -175,6 +182,7 @@ __global__ void __launch_bounds__(WilsonShape<PREC>::threads, WilsonShape<PREC>:
 
 #pragma unroll
   for (int mu = 0; mu < 4; ++mu) {
+    if (!FULLM && a.s == 0.0) break;  // hop mode without the hopping term
     // forward neighbour x + mu, link U_mu(x) stored at (mu, par, cb)
     {
       int y[4] = {x[0], x[1], x[2], x[3]};
@@ -234,13 +242,39 @@ __global__ void __launch_bounds__(WilsonShape<PREC>::threads, WilsonShape<PREC>:
         out[6 * s + 2 * c + 1] = fma(mk, acc[s][c].i, av[3 * s + c].i);
       }
   } else {
+    const T sc = (T)a.s;
+    C<T> v[12];
 #pragma unroll
     for (int s = 0; s < 4; ++s)
 #pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        out[6 * s + 2 * c] = acc[s][c].r;
-        out[6 * s + 2 * c + 1] = acc[s][c].i;
+      for (int c = 0; c < 3; ++c) v[3 * s + c] = sc * acc[s][c];
+    const size_t pb = CloverIO<PREC>::parity_bytes(Vh);
+    if (a.self) {
+      T sl[24];
+      SpinorIO<PREC, 24>::load(a.self, Vh, cb, sl);
+      C<T> sv[12], cv[12];
+#pragma unroll
+      for (int k = 0; k < 12; ++k) sv[k] = C<T>{sl[2 * k], sl[2 * k + 1]};
+      if (a.c_self) {
+        apply_clover_site<PREC, T>(a.c_self + par * pb, Vh, cb, sv, cv);
+      } else {
+#pragma unroll
+        for (int k = 0; k < 12; ++k) cv[k] = sv[k];
       }
+#pragma unroll
+      for (int k = 0; k < 12; ++k) v[k] = v[k] + cv[k];
+    }
+    if (a.c_post) {
+      C<T> w[12];
+      apply_clover_site<PREC, T>(a.c_post + par * pb, Vh, cb, v, w);
+#pragma unroll
+      for (int k = 0; k < 12; ++k) v[k] = w[k];
+    }
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      out[2 * k] = v[k].r;
+      out[2 * k + 1] = v[k].i;
+    }
   }
   SpinorIO<PREC, 24>::store(dst, Vh, cb, out);
 }

@@ -24,7 +24,7 @@ ERR_NAMES = {0: "OK", -1: "ERR_ARG", -2: "ERR_CUDA", -3: "ERR_OOM", -4: "ERR_UNS
 WILSON_CLOVER, ASQTAD = 0, 1
 F64, F32, F16 = 0, 1, 2
 PARITY_FULL, PARITY_EVEN, PARITY_ODD = -1, 0, 1
-CG_NORMAL, CG_EVEN_NORMAL, BICGSTAB, GCR_DD, GCR = 0, 1, 2, 3, 4
+CG_NORMAL, CG_EVEN_NORMAL, BICGSTAB, GCR_DD, GCR, BICGSTAB_EO, GCR_EO = 0, 1, 2, 3, 4, 5, 6
 
 
 class DiracParams(ctypes.Structure):
@@ -69,6 +69,7 @@ _SIGS = {
     "dirac_apply_dagger": (_ci, [_vp, _vp, _vp, _ci, _ci, _vp]),
     "dirac_apply_normal": (_ci, [_vp, _vp, _vp, _ci, _ci, _vp]),
     "schwarz_precondition": (_ci, [_vp, _vp, _vp, _ci, _vp]),
+    "dirac_apply_eo": (_ci, [_vp, _vp, _vp, _ci, _ci, _vp]),
     "dirac_norm2": (_ci, [_vp, _vp, _ci, _ci, _pd, _vp]),
     "dirac_cdot": (_ci, [_vp, _vp, _vp, _ci, _ci, _pd, _vp]),
     "dirac_caxpy_norm": (_ci, [_vp, _cd, _cd, _vp, _vp, _ci, _ci, _pd, _vp]),
@@ -208,6 +209,10 @@ class Lattice:
     def apply_normal(self, out, inp, parity=PARITY_FULL, prec=F64, stream=None):
         return self.check(dirac_apply_normal(self.ctx, out.data_ptr(), inp.data_ptr(), parity,
                                              prec, _stream(stream)), "dirac_apply_normal")
+
+    def apply_eo(self, out, inp, prec=F64, dagger=False, stream=None):
+        return self.check(dirac_apply_eo(self.ctx, out.data_ptr(), inp.data_ptr(), prec, int(dagger),
+                                         _stream(stream)), "dirac_apply_eo")
 
     def schwarz(self, out, inp, prec=F16, stream=None):
         return self.check(schwarz_precondition(self.ctx, out.data_ptr(), inp.data_ptr(), prec,

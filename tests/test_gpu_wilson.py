@@ -117,3 +117,19 @@ def test_gamma5_hermiticity_on_gpu(dirac):
     a = lat.cdot(f[1], Mx, F64)
     b = lat.cdot(Mdy, f[0], F64)
     assert abs(a - b) < 1e-12 * abs(a)
+
+
+@pytest.mark.parametrize("prec", [F64, F32, F16])
+@pytest.mark.parametrize("dagger", [False, True])
+def test_schur_operator(dirac, prec, dagger):
+    """Even-odd Schur complement Ahat_ee - kappa^2 D_eo Ahat_oo^-1 D_oe (Sec. 3.1)."""
+    dims = (6, 6, 6, 10)
+    kappa = 0.13
+    lat, U, psi, Ud, Ad = _setup(dirac, dims, 3, prec, 12, kappa=kappa)
+    x = lat.to_device(psi.cuda(), prec, 0)
+    y = lat.new_field(prec, 0)
+    lat.apply_eo(y, x, prec, dagger)
+    got = lat.to_natural(y, prec, 0, device="cpu").numpy()
+    ev = parity_mask(dims, 0)
+    ref = wilson.apply_schur(Ud, Ad, kappa, dec_spinor(psi.numpy(), prec) * ev[..., None, None], True, dagger)
+    check(got[ev], ref[ev], prec, 24, f"Schur prec={prec} dag={dagger}")
