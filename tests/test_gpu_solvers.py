@@ -148,3 +148,20 @@ def test_not_converged_status(dirac):
     st = lat.solve(fx, fb, dirac.BICGSTAB, tol=1e-10, max_iter=3, raise_on_error=False)
     assert st["status"] == "ERR_NOT_CONVERGED" and st["iters"] == 3
     assert 0 < st["true_rel_resid"] < 1
+
+
+@pytest.mark.parametrize("alg", ["BICGSTAB", "GCR_DD", "CG_NORMAL", "BICGSTAB_EO"])
+def test_nonfinite_source_is_reported(dirac, alg):
+    """A NaN in the source is detected from the device-side scalars and reported as
+    DIRAC_ERR_NONFINITE (failure injected on the host side, in the data)."""
+    dims = (4, 4, 4, 4)
+    lat = dirac.Lattice(dims, dirac.WILSON_CLOVER, kappa=0.12, csw=1.0, block=(2, 2, 2, 2),
+                        recon=(18, 12, 12))
+    lat.load_gauge(synth.wilson_gauge(dims, 0.5, 1, 1))
+    b = synth.wilson_spinor(dims, 2)
+    b[1, 2, 3, 0, 1, 2] = float("nan")
+    fb = lat.to_device(b.cuda(), F64)
+    fx = lat.new_field(F64)
+    st = lat.solve(fx, fb, getattr(dirac, alg), tol=1e-10, max_iter=50, prec_sloppy=F32,
+                   prec_precond=F32, raise_on_error=False)
+    assert st["status"] == "ERR_NONFINITE", st
