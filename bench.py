@@ -211,6 +211,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer e2e timing")
     ap.add_argument("--no-asqtad", action="store_true", help="skip the asqtad rows")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched multi-RHS row")
     ap.add_argument("--asqtad-dims", type=int, nargs=4, default=[48, 48, 48, 144],
                     help="asqtad lattice (48^3x144 unless profiling a smaller case)")
     ap.add_argument("--dims", type=int, nargs=4, default=list(DIMS),
@@ -316,6 +317,8 @@ def main():
     del fields
     lat.close()
     torch.cuda.empty_cache()
+    if not args.no_batch:
+        rows["batched_multi_rhs"] = measure_batch(dirac, synth, dev, stream, peak)
     if not args.no_asqtad:
         ad = tuple(args.asqtad_dims)
         rows["asqtad_%dx%dx%dx%d" % ad] = measure_asqtad(dirac, synth, dev, stream, peak,
@@ -379,6 +382,81 @@ def measure_wilson_rows(lat, dirac, fields, precs, stream, peak):
                                         "GBps_incl_sync": round(3 * fb / (ms / 1e3) / 1e9, 1)}
     out["schwarz"]["fp32_peak_tflops"] = round(FP32_PEAK_TFLOPS, 1)
     return out
+
+
+BATCH_LATTICES = (((16, 16, 16, 32), 0.130, 4001), ((24, 24, 24, 64), 0.133, 4003),
+                  ((32, 32, 32, 64), 0.136, 4005))
+BATCH_RHS = 12
+# bytes per site of one batched application: per right-hand side spinor in + out
+# (FP16 52 + 52, FP32 96 + 96), once per site 4 links + the clover (FP16 96 + 148,
+# FP32 192 + 288)
+
+
+def measure_batch(dirac, synth, dev, stream, peak):
+    """12 right-hand sides on each of 16^3x32, 24^3x64, 32^3x64 (FP16 storage as
+    configured, and FP32): single-RHS launches vs one multi-RHS launch per lattice vs
+    one persistent launch over all lattices (autotuned) vs its CUDA-graph replay."""
+    return {name: measure_batch_prec(dirac, synth, dev, stream, peak, pid)
+            for name, pid in (("f16", dirac.F16), ("f32", dirac.F32))}
+
+
+def measure_batch_prec(dirac, synth, dev, stream, peak, prec):
+    import torch
+    pname = "f16" if prec == dirac.F16 else "f32"
+    shared = 96 + 148 if prec == dirac.F16 else 192 + 288
+    per_rhs = 104 if prec == dirac.F16 else 192
+    lats, ins, outs = [], [], []
+    for dims, kappa, seed in BATCH_LATTICES:
+        U = synth.wilson_gauge(dims, 0.5, 3, seed, device=dev)
+        lat = dirac.Lattice(dims, dirac.WILSON_CLOVER, kappa=kappa, csw=CSW, recon=(18, 12, 12),
+                            prec_mask=(1 << dirac.F64) | (1 << prec))
+        lat.load_gauge(U)
+        fb = lat.field_bytes(prec)
+        x = torch.empty(BATCH_RHS * fb, dtype=torch.uint8, device=dev)
+        for r in range(BATCH_RHS):
+            lat.import_spinor(x[r * fb:(r + 1) * fb], prec, -1,
+                              synth.wilson_spinor(dims, seed + 1 + r, device=dev))
+        lats.append(lat)
+        ins.append(x)
+        outs.append(torch.empty_like(x))
+    torch.cuda.synchronize()
+    sites = sum(l.volume for l in lats)
+    alg_bytes = sum(l.volume * (BATCH_RHS * per_rhs + shared) for l in lats)
+    single_bytes = sites * BATCH_RHS * SITE_BYTES[pname]
+
+    def single():
+        for lat, x, y in zip(lats, ins, outs):
+            fb = lat.field_bytes(prec)
+            for r in range(BATCH_RHS):
+                lat.apply(y[r * fb:(r + 1) * fb], x[r * fb:(r + 1) * fb], dirac.PARITY_FULL, prec, stream)
+
+    def multi():
+        for lat, x, y in zip(lats, ins, outs):
+            lat.apply_multi(y, x, BATCH_RHS, prec, stream)
+
+    res = {"lattices": [list(d) for d, _, _ in BATCH_LATTICES], "rhs_per_lattice": BATCH_RHS,
+           "sites": sites, "alg_bytes_per_application": alg_bytes}
+    for name, fn, n in (("single_rhs_launches", single, 10), ("multi_rhs_per_lattice", multi, 20)):
+        ms = _event_time(fn, n, stream)
+        res[name] = {"ms": round(ms, 4), "site_rhs_per_s": round(sites * BATCH_RHS / (ms / 1e3) / 1e9, 3),
+                     "alg_GBps": round(alg_bytes / (ms / 1e3) / 1e9, 1)}
+    b = dirac.Batch(lats, outs, ins, [BATCH_RHS] * len(lats), prec, stream)
+    ms = _event_time(b.apply, 20, stream)
+    res["persistent_batched"] = {"ms": round(ms, 4), **b.info(),
+                                 "site_rhs_per_s": round(sites * BATCH_RHS / (ms / 1e3) / 1e9, 3),
+                                 "alg_GBps": round(alg_bytes / (ms / 1e3) / 1e9, 1),
+                                 "frac_of_hbm": round(alg_bytes / (ms / 1e3) / 1e9 / peak, 4),
+                                 "single_rhs_equiv_GBps": round(single_bytes / (ms / 1e3) / 1e9, 1)}
+    napply = 10
+    b.capture(napply, stream)
+    ms = _event_time(b.apply, 5, stream) / napply
+    res["graph_replay"] = {"napply": napply, "ms_per_application": round(ms, 4),
+                           "alg_GBps": round(alg_bytes / (ms / 1e3) / 1e9, 1)}
+    res["speedup_vs_single_rhs"] = round(res["single_rhs_launches"]["ms"] / res["persistent_batched"]["ms"], 3)
+    b.close()
+    for lat in lats:
+        lat.close()
+    return res
 
 
 MS_SHIFTS = (0.0, 0.0005, 0.005, 0.05)

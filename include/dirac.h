@@ -128,6 +128,30 @@ int dirac_apply_normal(dirac_ctx* ctx, void* out, const void* in, dirac_parity p
  * with Ahat^-1 built alongside Ahat by dirac_load_gauge. Wilson-clover only. */
 int dirac_apply_eo(dirac_ctx* ctx, void* out, const void* in, dirac_prec prec, int dagger, void* stream);
 
+/* Batched Wilson-clover operator (many right-hand sides, several lattices per launch).
+ * The paper applies M to one right-hand side at a time; batching reuses each site's
+ * links and clover across the right-hand sides of a tile (read from DRAM once).
+ *
+ * dirac_apply_multi: out_r = M in_r for r < nrhs on one lattice; in and out each hold
+ * nrhs consecutive full fields (dirac_field_bytes(ctx, prec, FULL) apart), no overlap.
+ *
+ * dirac_batch_create: a plan applying M of ctxs[l] to nrhs[l] consecutive full fields
+ * in[l] -> out[l] for l < nlat (1..16 lattices of any sizes; one precision, the same
+ * link compression) in ONE persistent launch. Creating the plan autotunes the tile
+ * shape (right-hand sides per CTA x resident CTAs per SM) by timing each candidate on
+ * `stream` (it writes `out`), then synchronises. dirac_batch_capture records napply
+ * launches in a CUDA graph; afterwards dirac_batch_apply replays the graph (napply
+ * applications) instead of one direct launch. The plan keeps the pointers it was given. */
+typedef struct dirac_batch dirac_batch;
+int dirac_apply_multi(dirac_ctx* ctx, void* out, const void* in, int nrhs, dirac_prec prec, void* stream);
+int dirac_batch_create(dirac_ctx* const* ctxs, int nlat, void* const* out, const void* const* in,
+                       const int* nrhs, dirac_prec prec, void* stream, dirac_batch** plan);
+int dirac_batch_apply(dirac_batch* plan, void* stream);
+int dirac_batch_capture(dirac_batch* plan, int napply, void* stream);
+int dirac_batch_info(const dirac_batch* plan, int* rhs_per_cta, int* ctas_per_sm, int* grid,
+                     double* tuned_ms);
+int dirac_batch_destroy(dirac_batch* plan);
+
 /* out = K in: the non-overlapping additive Schwarz preconditioner of Sec. 3.2 / 8.1
  * for the Wilson-clover operator. On every block (params.block) the operator with
  * Dirichlet (zero) block boundaries is solved by params.mr_steps minimal-residual
@@ -201,7 +225,7 @@ typedef struct {
   int iters, restarts, reliable_updates, dslash_calls, precond_calls;
   double true_rel_resid;   /* final ||b - A x|| / ||b|| recomputed in FP64 */
   double seconds;          /* wall time of the solve including the final sync */
-  double flops;            /* operator + BLAS flops by the counts in the design doc */
+  double flops;            /* operator + preconditioner + BLAS flops from per-site counts */
 } dirac_solver_stats;
 
 /* Solve A x = b in FP64 (A = M, M^dagger M or (M^dagger M)_ee per alg). x and b are

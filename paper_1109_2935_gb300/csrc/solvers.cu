@@ -345,6 +345,7 @@ int solve_cg(Ctx& S, char* x, const char* b, const dirac_solver_params& P) {
   if (!r || !rs || !p || !Ap || !xs) return set_err(S.c, DIRAC_ERR_OOM, "solver workspace");
   double bb;
   BT(blas_norm2(B, S.f(b, P64), &bb, S.st));
+  if (!finite(bb)) return set_err(S.c, DIRAC_ERR_NONFINITE, "non-finite source");
   if (bb == 0.0) {
     BT(blas_zero(B, S.f(x, P64), S.st));
     return DIRAC_OK;
@@ -404,6 +405,7 @@ int solve_bicgstab(Ctx& S, char* x, const char* b, const dirac_solver_params& P)
   if (!r || !rs || !r0 || !p || !v || !t || !xs) return set_err(S.c, DIRAC_ERR_OOM, "solver workspace");
   double bb;
   BT(blas_norm2(B, S.f(b, P64), &bb, S.st));
+  if (!finite(bb)) return set_err(S.c, DIRAC_ERR_NONFINITE, "non-finite source");
   if (bb == 0.0) {
     BT(blas_zero(B, S.f(x, P64), S.st));
     return DIRAC_OK;
@@ -490,6 +492,7 @@ int solve_gcr(Ctx& S, char* x, const char* b, const dirac_solver_params& P, bool
 
   double bb;
   BT(blas_norm2(B, S.f(b, P64), &bb, S.st));
+  if (!finite(bb)) return set_err(S.c, DIRAC_ERR_NONFINITE, "non-finite source");
   if (bb == 0.0) {
     BT(blas_zero(B, S.f(x, P64), S.st));
     return DIRAC_OK;
@@ -595,6 +598,7 @@ int solve_ms_stage(Ctx& S, char* const* xout, const char* b, const double* shift
   if (!rs || !Ap) return set_err(S.c, DIRAC_ERR_OOM, "solver workspace");
   double bb;
   BT(blas_norm2(B, S.f(b, P64), &bb, S.st));
+  if (!finite(bb)) return set_err(S.c, DIRAC_ERR_NONFINITE, "non-finite source");
   if (bb == 0.0) {
     for (int j = 0; j < n; ++j) BT(blas_zero(B, S.f(xout[j], P64), S.st));
     return DIRAC_OK;
@@ -683,6 +687,10 @@ int finish_stats(Ctx& S, const char* x, const char* b, double tol) {
   S.stats->flops -= S.flops_per_apply;
   rc = blas_xmy_norm(S.c->blas, S.f(b, P64), S.f(r, P64), &rr, S.st);
   if (rc) return set_err(S.c, rc, blas_error(S.c->blas));
+  if (!std::isfinite(bb) || !std::isfinite(rr)) {
+    S.stats->true_rel_resid = NAN;
+    return set_err(S.c, DIRAC_ERR_NONFINITE, "non-finite true residual");
+  }
   S.stats->true_rel_resid = bb > 0 ? std::sqrt(rr / bb) : 0.0;
   if (!std::isfinite(S.stats->true_rel_resid)) return set_err(S.c, DIRAC_ERR_NONFINITE, "non-finite true residual");
   if (S.stats->true_rel_resid > tol) return set_err(S.c, DIRAC_ERR_NOT_CONVERGED, "max_iter reached");

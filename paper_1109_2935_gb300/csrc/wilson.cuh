@@ -135,13 +135,13 @@ template <int PREC> struct WilsonShape { static constexpr int threads = 64, minb
 template <> struct WilsonShape<P32> { static constexpr int threads = 64, minb = 8; };
 template <> struct WilsonShape<P64> { static constexpr int threads = 128, minb = 1; };
 
+// One output site of the stencil: thread index idx over the Vh (hop mode) or 2 Vh
+// (full operator) output sites. Shared by the single-RHS, multi-RHS and batched kernels.
 template <int PREC, int R, bool FULLM>
-__global__ void __launch_bounds__(WilsonShape<PREC>::threads, WilsonShape<PREC>::minb)
-    wilson_kernel(const WilsonArg a) {
+__device__ __forceinline__ void wilson_site(const WilsonArg& a, int idx) {
   using T = typename Real<PREC>::T;
   const Geom& g = a.g;
   const int Vh = g.Vh;
-  int idx = blockIdx.x * blockDim.x + threadIdx.x;
   int par, cb;
   if (FULLM) {
     // The two parities alternate every WILSON_INTERLEAVE threads (a warp: the parity
@@ -277,6 +277,12 @@ __global__ void __launch_bounds__(WilsonShape<PREC>::threads, WilsonShape<PREC>:
     }
   }
   SpinorIO<PREC, 24>::store(dst, Vh, cb, out);
+}
+
+template <int PREC, int R, bool FULLM>
+__global__ void __launch_bounds__(WilsonShape<PREC>::threads, WilsonShape<PREC>::minb)
+    wilson_kernel(const WilsonArg a) {
+  wilson_site<PREC, R, FULLM>(a, blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 template <int PREC>

@@ -70,6 +70,14 @@ _SIGS = {
     "dirac_apply_normal": (_ci, [_vp, _vp, _vp, _ci, _ci, _vp]),
     "schwarz_precondition": (_ci, [_vp, _vp, _vp, _ci, _vp]),
     "dirac_apply_eo": (_ci, [_vp, _vp, _vp, _ci, _ci, _vp]),
+    "dirac_apply_multi": (_ci, [_vp, _vp, _vp, _ci, _ci, _vp]),
+    "dirac_batch_create": (_ci, [ctypes.POINTER(_vp), _ci, ctypes.POINTER(_vp), ctypes.POINTER(_vp),
+                                 ctypes.POINTER(_ci), _ci, _vp, ctypes.POINTER(_vp)]),
+    "dirac_batch_apply": (_ci, [_vp, _vp]),
+    "dirac_batch_capture": (_ci, [_vp, _ci, _vp]),
+    "dirac_batch_info": (_ci, [_vp, ctypes.POINTER(_ci), ctypes.POINTER(_ci), ctypes.POINTER(_ci),
+                               ctypes.POINTER(ctypes.c_double)]),
+    "dirac_batch_destroy": (_ci, [_vp]),
     "dirac_norm2": (_ci, [_vp, _vp, _ci, _ci, _pd, _vp]),
     "dirac_cdot": (_ci, [_vp, _vp, _vp, _ci, _ci, _pd, _vp]),
     "dirac_caxpy_norm": (_ci, [_vp, _cd, _cd, _vp, _vp, _ci, _ci, _pd, _vp]),
@@ -214,6 +222,11 @@ class Lattice:
         return self.check(dirac_apply_eo(self.ctx, out.data_ptr(), inp.data_ptr(), prec, int(dagger),
                                          _stream(stream)), "dirac_apply_eo")
 
+    def apply_multi(self, out, inp, nrhs, prec=F16, stream=None):
+        """out_r = M in_r for nrhs consecutive full fields in `inp` / `out`."""
+        return self.check(dirac_apply_multi(self.ctx, out.data_ptr(), inp.data_ptr(), nrhs, prec,
+                                            _stream(stream)), "dirac_apply_multi")
+
     def schwarz(self, out, inp, prec=F16, stream=None):
         return self.check(schwarz_precondition(self.ctx, out.data_ptr(), inp.data_ptr(), prec,
                                                _stream(stream)), "schwarz_precondition")
@@ -269,3 +282,48 @@ class Lattice:
             raise DiracError(rc, f"solve_multishift: {dirac_last_error(self.ctx).decode()}")
         return {"status": ERR_NAMES.get(rc, rc), "multishift": st[0].as_dict(),
                 "refine": [st[1 + j].as_dict() for j in range(n)]}
+
+
+class Batch:
+    """A batched-operator plan over several lattices (dirac_batch_*): M of each lattice
+    applied to its consecutive right-hand sides in one persistent launch."""
+
+    def __init__(self, lattices, outs, ins, nrhs, prec=F16, stream=None):
+        n = len(lattices)
+        self.keep = (lattices, outs, ins)
+        ctxs = (_vp * n)(*[l.ctx.value if hasattr(l.ctx, "value") else l.ctx for l in lattices])
+        o = (_vp * n)(*[t.data_ptr() for t in outs])
+        i = (_vp * n)(*[t.data_ptr() for t in ins])
+        r = (_ci * n)(*nrhs)
+        h = _vp()
+        rc = dirac_batch_create(ctxs, n, o, i, r, prec, _stream(stream), ctypes.byref(h))
+        if rc != OK:
+            raise DiracError(rc, "dirac_batch_create failed")
+        self.plan = h
+
+    def info(self):
+        rg, per, grid, ms = _ci(), _ci(), _ci(), ctypes.c_double()
+        dirac_batch_info(self.plan, ctypes.byref(rg), ctypes.byref(per), ctypes.byref(grid), ctypes.byref(ms))
+        return {"rhs_per_cta": rg.value, "ctas_per_sm": per.value, "grid": grid.value,
+                "tuned_ms": ms.value}
+
+    def apply(self, stream=None):
+        rc = dirac_batch_apply(self.plan, _stream(stream))
+        if rc != OK:
+            raise DiracError(rc, "dirac_batch_apply failed")
+
+    def capture(self, napply, stream=None):
+        rc = dirac_batch_capture(self.plan, napply, _stream(stream))
+        if rc != OK:
+            raise DiracError(rc, "dirac_batch_capture failed")
+
+    def close(self):
+        if self.plan:
+            dirac_batch_destroy(self.plan)
+            self.plan = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
