@@ -205,7 +205,10 @@ typedef enum {
   DIRAC_SOLVER_GCR = 4,            /* GCR of Algorithm 1 with K = 1 */
   DIRAC_SOLVER_BICGSTAB_EO = 5,    /* BiCGstab on the even-odd Schur system (Sec. 3.1), then
                                       x_o = Ahat_oo^-1 (b_o + kappa D_oe x_e); x, b full fields */
-  DIRAC_SOLVER_GCR_EO = 6          /* unpreconditioned GCR on the even-odd Schur system */
+  DIRAC_SOLVER_GCR_EO = 6,         /* unpreconditioned GCR on the even-odd Schur system */
+  DIRAC_SOLVER_GCR_PTC = 7         /* GCR of Algorithm 1 with K = the attached PTC network, or
+                                      the Schwarz preconditioner when that reduces the
+                                      initial residual more (dirac_ptc_attach) */
 } dirac_solver;
 
 typedef struct {
@@ -226,6 +229,8 @@ typedef struct {
   double true_rel_resid;   /* final ||b - A x|| / ||b|| recomputed in FP64 */
   double seconds;          /* wall time of the solve including the final sync */
   double flops;            /* operator + preconditioner + BLAS flops from per-site counts */
+  int precond_kind;        /* preconditioner used: 0 none, 1 Schwarz, 2 PTC network */
+  double precond_reduction[2]; /* GCR_PTC: ||r0 - M K r0|| / ||r0|| of K = Schwarz, PTC */
 } dirac_solver_stats;
 
 /* Solve A x = b in FP64 (A = M, M^dagger M or (M^dagger M)_ee per alg). x and b are
@@ -247,6 +252,68 @@ int solve(dirac_ctx* ctx, void* x, const void* b, const dirac_solver_params* par
  * Returns DIRAC_ERR_NOT_CONVERGED if some refinement ran out of iterations. */
 int solve_multishift(dirac_ctx* ctx, void* const* x, const void* b, const double* shifts, int nshift,
                      const dirac_solver_params* params, dirac_solver_stats* stats, void* stream);
+
+/* ------------------------------------------------------------------ learned preconditioner
+ * A gauge-equivariant parallel-transport convolution (PTC) network K, a learned
+ * preconditioner for the flexible GCR of Algorithm 1 (whose outer iteration accepts any
+ * preconditioner, Sec. 3.2). The paper has no such network: this is an extension. Layer
+ * l maps channels_in = channels[l-1] spinor fields to channels[l] fields:
+ *   out_c(x) = sum_c' sum_p W_l[p][c][c'] (T_p in_c')(x),  p = 0, +x, -x, +y, ..., -t
+ *   T_0 = 1, (T_+mu f)(x) = U_mu(x) f(x+mu), (T_-mu f)(x) = U_mu(x-mu)^dagger f(x-mu)
+ * with W a complex 4x4 spin matrix (colour untouched, so K commutes with gauge
+ * transformations), the fermion boundary sign on hops across an antiperiodic t edge,
+ * and no nonlinearity (K is linear). Weights are FP32 complex, stored per layer as
+ * [p (9)][c_out][c_in][s (4)][s' (4)], (re, im) interleaved; on the host they are
+ * passed as FP64 (re, im) pairs in the same order, layers consecutive.
+ * Fields are FP32 full fields in the device layout of the context (dirac_field_bytes
+ * with DIRAC_PREC_F32, parity FULL); the context must keep FP32 (prec_mask bit 1) and
+ * be a Wilson-clover context with its gauge field loaded. */
+typedef struct dirac_ptc dirac_ptc;
+typedef struct {
+  int layers;          /* 1..4 */
+  int channels[5];     /* channels[0] = channels[layers] = 1; the others 1, 2 or 4 */
+} dirac_ptc_params;
+
+typedef struct {
+  int steps;           /* Adam steps */
+  int batch;           /* pairs per step, 1..16 */
+  double lr, beta1, beta2, eps;  /* Adam (Kingma and Ba): step lr, moment decays, eps */
+  unsigned seed;       /* order in which pairs are visited (epochs reshuffled) */
+} dirac_ptc_train_params;
+
+/* Create a network on ctx whose layers pass channel 0 through on the local path (K = 1;
+ * hidden channels zero: a caller that trains sets perturbed initial weights first, or
+ * the zero channels stay zero). The context owns it: dirac_destroy destroys networks
+ * still alive. Returns DIRAC_ERR_ARG for bad channel lists,
+ * DIRAC_ERR_UNSUPPORTED for an asqtad context or one without FP32. */
+int dirac_ptc_create(dirac_ctx* ctx, const dirac_ptc_params* params, dirac_ptc** net);
+/* Number of complex weights (sum over layers of 9 * 16 * c_out * c_in). */
+long long dirac_ptc_num_weights(const dirac_ptc* net);
+/* Copy n (= dirac_ptc_num_weights) complex weights from / to host memory, FP64 pairs. */
+int dirac_ptc_set_weights(dirac_ptc* net, const double* w, long long n);
+int dirac_ptc_get_weights(const dirac_ptc* net, double* w, long long n);
+/* out = K in (FP32 full fields, distinct; asynchronous on stream). */
+int dirac_ptc_apply(dirac_ptc* net, void* out, const void* in, void* stream);
+/* Loss L = ||K r - v||^2 / ||v||^2 of one pair and its derivative with respect to the
+ * conjugate weights, dL/dconj(W), into grad (host, FP64 pairs, num_weights entries);
+ * loss and grad may be NULL. Synchronises stream. */
+int dirac_ptc_gradient(dirac_ptc* net, const void* r, const void* v, double* loss, double* grad,
+                       void* stream);
+/* Train on pairs (r_i, v_i), i < npairs: Adam on the mean over a batch of
+ * ||K r_i - v_i||^2 / ||v_i||^2. r may be NULL: then r_i = M v_i is computed (FP32)
+ * by the library. r[i], v[i]: FP32 full fields owned by the caller, unchanged.
+ * loss (host, may be NULL): params->steps entries, the batch loss before each step.
+ * Synchronises stream. */
+int dirac_ptc_train(dirac_ptc* net, const void* const* r, const void* const* v, int npairs,
+                    const dirac_ptc_train_params* params, double* loss, void* stream);
+/* Make net the preconditioner of DIRAC_SOLVER_GCR_PTC on ctx (NULL detaches). With
+ * force = 0, every such solve starts by applying both the network and the Schwarz
+ * preconditioner to the initial residual r0 and keeps the one with the smaller
+ * ||r0 - M K r0|| (Schwarz is the fallback); force = 1 always uses the network. stats
+ * report the choice and, with force = 0, both reductions. */
+int dirac_ptc_attach(dirac_ctx* ctx, dirac_ptc* net, int force);
+/* Free the network (detaching it first). NULL is a no-op. */
+int dirac_ptc_destroy(dirac_ptc* net);
 
 #ifdef __cplusplus
 }

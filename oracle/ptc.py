@@ -11,7 +11,8 @@ Layer (channels c_in -> c_out), for spinor fields psi_c(x) (4 spins x 3 colours)
 with W[p, c, c'] a complex 4x4 matrix acting on spin only and the fermion boundary
 sign on hops across an antiperiodic t boundary. Because W does not touch colour and
 T_p transports colour, the layer commutes with gauge transformations. The network is
-two layers, 1 -> h -> 1 channels, linear: K(r) = L2(L1(r)).
+a chain of such layers from 1 channel back to 1 (e.g. 1 -> 2 -> 1), linear:
+K(r) = L_n(... L_1(r)).
 
 Path order: p = 0, then (+mu, -mu) for mu = x, y, z, t, i.e. index 1 + 2 mu + (0|1).
 Loss for a pair (r, v): |K(r) - v|^2 / |v|^2. For a real loss of complex weights the
@@ -84,21 +85,29 @@ def layer_backward(U, W, xs, gys, antiperiodic_t=True):
     return gxs, gW
 
 
-def net_forward(U, W1, W2, r, antiperiodic_t=True):
-    h = layer_forward(U, W1, [r], antiperiodic_t)
-    return layer_forward(U, W2, h, antiperiodic_t)[0], h
+def net_forward(U, Ws, r, antiperiodic_t=True):
+    """K(r) for the layers Ws (first takes 1 channel, last gives 1); also returns every
+    layer's output (activations[l] = output of layer l, activations[-1] = K(r))."""
+    acts = []
+    h = [r]
+    for W in Ws:
+        h = layer_forward(U, W, h, antiperiodic_t)
+        acts.append(h)
+    return h[0], acts
 
 
-def loss_and_grad(U, W1, W2, r, v, antiperiodic_t=True):
-    """L = |K(r) - v|^2 / |v|^2 and its conjugate derivatives w.r.t. W1, W2."""
-    k, h = net_forward(U, W1, W2, r, antiperiodic_t)
+def loss_and_grad(U, Ws, r, v, antiperiodic_t=True):
+    """L = |K(r) - v|^2 / |v|^2 and its conjugate derivatives w.r.t. every layer's W."""
+    k, acts = net_forward(U, Ws, r, antiperiodic_t)
     vv = float(np.vdot(v, v).real)
     d = k - v
     L = float(np.vdot(d, d).real) / vv
-    gk = d / vv  # dL/dconj(K(r))
-    gh, gW2 = layer_backward(U, W2, h, [gk], antiperiodic_t)
-    _, gW1 = layer_backward(U, W1, [r], gh, antiperiodic_t)
-    return L, gW1, gW2
+    g = [d / vv]  # dL/dconj(K(r))
+    grads = [None] * len(Ws)
+    for l in range(len(Ws) - 1, -1, -1):
+        xin = [r] if l == 0 else acts[l - 1]
+        g, grads[l] = layer_backward(U, Ws[l], xin, g, antiperiodic_t)
+    return L, grads
 
 
 def identity_weights(c_out, c_in, scale=1.0):

@@ -255,6 +255,9 @@ int dirac_create(const dirac_params* params, dirac_ctx** out) {
 int dirac_destroy(dirac_ctx* c) {
   if (!c) return DIRAC_ERR_ARG;
   bool ok = true;
+  for (dirac_ptc* n : c->ptcs) ptc_release(n);
+  c->ptcs.clear();
+  c->ptc_attached = nullptr;
   auto fr = [&](void* p) { if (p && cudaFree(p) != cudaSuccess) ok = false; };
   for (int q = 0; q < 3; ++q)
     for (char* p : {c->gauge[q], c->fat[q], c->clover[q], c->clover_inv[q], c->tmp[q], c->tmp2[q]}) fr(p);

@@ -5,6 +5,7 @@
 #include <cstddef>
 #include <cstdint>
 #include <string>
+#include <vector>
 
 #include "../../include/dirac.h"
 #include "field.cuh"
@@ -136,6 +137,12 @@ int schwarz_apply(dirac_ctx* c, char* out, const char* in, int prec, cudaStream_
 int schur_source(dirac_ctx* c, char* bhat, const char* b, int prec, cudaStream_t st);
 int schur_reconstruct(dirac_ctx* c, char* x, const char* b, int prec, cudaStream_t st);
 
+// ---------------------------------------------------------------- PTC network (ptc.cu)
+// out = K in on FP32 full fields; flops of one application; free a network
+int ptc_apply_internal(dirac_ptc* n, char* out, const char* in, cudaStream_t st);
+double ptc_flops_per_apply(const dirac_ptc* n);
+void ptc_release(dirac_ptc* n);
+
 }  // namespace dirac
 
 // ---------------------------------------------------------------- the context
@@ -165,5 +172,10 @@ struct dirac_ctx {
   // device staging for natural-layout spinors passed from host memory
   char* staging = nullptr;
   size_t staging_bytes = 0;
+  // PTC networks created on this context (freed by dirac_destroy) and the one
+  // DIRAC_SOLVER_GCR_PTC uses
+  std::vector<dirac_ptc*> ptcs;
+  dirac_ptc* ptc_attached = nullptr;
+  int ptc_force = 0;
   std::string err;
 };

@@ -468,11 +468,39 @@ int solve_bicgstab(Ctx& S, char* x, const char* b, const dirac_solver_params& P)
 }
 
 // ------------------------------------------------------------------ GCR (Algorithm 1)
-int solve_gcr(Ctx& S, char* x, const char* b, const dirac_solver_params& P, bool precond) {
+// Preconditioner K of the flexible GCR: none, the Schwarz preconditioner (runs in
+// prec_precond) or the attached PTC network (runs in FP32). A preconditioner whose
+// precision differs from the sloppy one gets its input and output converted.
+enum : int { K_NONE = 0, K_SCHWARZ = 1, K_PTC = 2, K_SELECT = 3 };
+
+struct Precond {
+  char* in[3] = {};
+  char* out[3] = {};
+  double flops[3] = {};
+};
+
+int precond_apply(Ctx& S, Precond& K, int kind, char* out, const char* in, int sp, int pp) {
+  Blas* B = S.c->blas;
+  const int kp = kind == K_PTC ? P32 : pp;
+  S.stats->precond_calls++;
+  S.stats->flops += K.flops[kind];
+  auto run = [&](char* o, const char* i) -> int {
+    return kind == K_PTC ? ptc_apply_internal(S.c->ptc_attached, o, i, S.st) : schwarz_apply(S.c, o, i, kp, S.st);
+  };
+  if (kp == sp) return run(out, in);
+  BT(blas_copy(B, S.f(K.in[kp], kp), S.f(in, sp), S.st));
+  TRY(run(K.out[kp], K.in[kp]));
+  BT(blas_copy(B, S.f(out, sp), S.f(K.out[kp], kp), S.st));
+  return DIRAC_OK;
+}
+
+int solve_gcr(Ctx& S, char* x, const char* b, const dirac_solver_params& P, int precond) {
   Blas* B = S.c->blas;
   const int sp = P.prec_sloppy, pp = P.prec_precond;
   const int kmax = P.k_max;
   if (kmax < 1 || kmax > KMAX) return set_err(S.c, DIRAC_ERR_ARG, "k_max must be in [1, 20]");
+  if (precond == K_SELECT && !S.c->ptc_attached)
+    return set_err(S.c, DIRAC_ERR_STATE, "GCR_PTC: no PTC network attached");
   char* r = S.get(P64);
   char* rh = S.get(sp);
   std::vector<char*> pv(kmax), zv(kmax);
@@ -480,11 +508,16 @@ int solve_gcr(Ctx& S, char* x, const char* b, const dirac_solver_params& P, bool
     pv[i] = S.get(sp);
     zv[i] = S.get(sp);
   }
-  char *pin = nullptr, *pout = nullptr;
-  if (precond && pp != sp) {
-    pin = S.get(pp);
-    pout = S.get(pp);
-    if (!pin || !pout) return set_err(S.c, DIRAC_ERR_OOM, "solver workspace");
+  Precond K;
+  K.flops[K_SCHWARZ] = (double)S.c->V * S.c->p.mr_steps * (1872.0 + 192.0);
+  if (precond == K_SELECT) K.flops[K_PTC] = ptc_flops_per_apply(S.c->ptc_attached);
+  for (int kind : {K_SCHWARZ, K_PTC}) {
+    if (precond == K_NONE || (precond != K_SELECT && precond != kind)) continue;
+    const int kp = kind == K_PTC ? P32 : pp;
+    if (kp == sp || K.in[kp]) continue;
+    K.in[kp] = S.get(kp);
+    K.out[kp] = S.get(kp);
+    if (!K.in[kp] || !K.out[kp]) return set_err(S.c, DIRAC_ERR_OOM, "solver workspace");
   }
   if (!r || !rh) return set_err(S.c, DIRAC_ERR_OOM, "solver workspace");
   for (int i = 0; i < kmax; ++i)
@@ -501,22 +534,29 @@ int solve_gcr(Ctx& S, char* x, const char* b, const dirac_solver_params& P, bool
   double r0n2;
   TRY(start_residual(S, x, b, r, P, bb, &r0n2));
   BT(blas_copy(B, S.f(rh, sp), S.f(r, P64), S.st));
+  int kind = precond;
+  if (precond == K_SELECT && S.c->ptc_force) {
+    kind = K_PTC;
+  } else if (precond == K_SELECT) {
+    // keep the preconditioner with the smaller ||r0 - M K r0|| on this source
+    for (int k2 : {K_SCHWARZ, K_PTC}) {
+      double e2;
+      TRY(precond_apply(S, K, k2, pv[0], rh, sp, pp));
+      TRY(S.A(zv[0], pv[0], sp));
+      BT(blas_xmy_norm(B, S.f(rh, sp), S.f(zv[0], sp), &e2, S.st));
+      S.stats->precond_reduction[k2 - 1] = r0n2 > 0 ? std::sqrt(e2 / r0n2) : 0.0;
+    }
+    const double* red = S.stats->precond_reduction;
+    kind = finite(red[1]) && red[1] < red[0] ? K_PTC : K_SCHWARZ;
+  }
+  S.stats->precond_kind = kind;
   KC((k_init<<<1, 1, 0, S.st>>>(S.S)));
-  const double sflops = (double)S.c->V * S.c->p.mr_steps * (1872.0 + 192.0);
   auto gb = [&](int i, int k) { return S.slot(S_GB + 4 * (i * KMAX + k) + 1); };
   int k = 0;
   while (r0n2 > target && S.stats->iters < P.max_iter) {
     // p_k = K r_k
-    if (precond) {
-      S.stats->precond_calls++;
-      S.stats->flops += sflops;
-      if (pp == sp) {
-        TRY(schwarz_apply(S.c, pv[k], rh, sp, S.st));
-      } else {
-        BT(blas_copy(B, S.f(pin, pp), S.f(rh, sp), S.st));
-        TRY(schwarz_apply(S.c, pout, pin, pp, S.st));
-        BT(blas_copy(B, S.f(pv[k], sp), S.f(pout, pp), S.st));
-      }
+    if (kind != K_NONE) {
+      TRY(precond_apply(S, K, kind, pv[k], rh, sp, pp));
     } else {
       BT(blas_copy(B, S.f(pv[k], sp), S.f(rh, sp), S.st));
     }
@@ -780,7 +820,8 @@ extern "C" int solve(dirac_ctx* c, void* x, const void* b, const dirac_solver_pa
     case DIRAC_SOLVER_BICGSTAB:
     case DIRAC_SOLVER_GCR: which = 0; break;
     case DIRAC_SOLVER_GCR_DD:
-      if (!wil) return set_err(c, DIRAC_ERR_UNSUPPORTED, "GCR_DD needs the Wilson-clover operator");
+    case DIRAC_SOLVER_GCR_PTC:
+      if (!wil) return set_err(c, DIRAC_ERR_UNSUPPORTED, "GCR_DD / GCR_PTC need the Wilson-clover operator");
       which = 0; break;
     default: return set_err(c, DIRAC_ERR_ARG, "unknown solver");
   }
@@ -788,7 +829,9 @@ extern "C" int solve(dirac_ctx* c, void* x, const void* b, const dirac_solver_pa
   int rc;
   if ((rc = check_op(c, P64, false))) return rc;
   if ((rc = check_op(c, P.prec_sloppy, false))) return rc;
-  if (P.alg == DIRAC_SOLVER_GCR_DD && (rc = check_op(c, P.prec_precond, false))) return rc;
+  if ((P.alg == DIRAC_SOLVER_GCR_DD || P.alg == DIRAC_SOLVER_GCR_PTC) && (rc = check_op(c, P.prec_precond, false)))
+    return rc;
+  if (P.alg == DIRAC_SOLVER_GCR_PTC && (rc = check_op(c, P32, false))) return rc;
   if ((rc = ensure_scalars(c))) return rc;
   dirac_solver_stats local{};
   dirac_solver_stats* st = stats ? stats : &local;
@@ -811,7 +854,7 @@ extern "C" int solve(dirac_ctx* c, void* x, const void* b, const dirac_solver_pa
     else rc = schur_source(c, bhat, (const char*)b, P64, s);
     if (rc == DIRAC_OK) {
       if (P.alg == DIRAC_SOLVER_BICGSTAB_EO) rc = solve_bicgstab(S, (char*)x, bhat, P);
-      else rc = solve_gcr(S, (char*)x, bhat, P, false);
+      else rc = solve_gcr(S, (char*)x, bhat, P, K_NONE);
     }
     if (rc == DIRAC_OK) rc = schur_reconstruct(c, (char*)x, (const char*)b, P64, s);
     // the final check is on the full system M x = b
@@ -823,8 +866,9 @@ extern "C" int solve(dirac_ctx* c, void* x, const void* b, const dirac_solver_pa
       case DIRAC_SOLVER_CG_NORMAL:
       case DIRAC_SOLVER_CG_EVEN_NORMAL: rc = solve_cg(S, (char*)x, (const char*)b, P); break;
       case DIRAC_SOLVER_BICGSTAB: rc = solve_bicgstab(S, (char*)x, (const char*)b, P); break;
-      case DIRAC_SOLVER_GCR_DD: rc = solve_gcr(S, (char*)x, (const char*)b, P, true); break;
-      default: rc = solve_gcr(S, (char*)x, (const char*)b, P, false); break;
+      case DIRAC_SOLVER_GCR_DD: rc = solve_gcr(S, (char*)x, (const char*)b, P, K_SCHWARZ); break;
+      case DIRAC_SOLVER_GCR_PTC: rc = solve_gcr(S, (char*)x, (const char*)b, P, K_SELECT); break;
+      default: rc = solve_gcr(S, (char*)x, (const char*)b, P, K_NONE); break;
     }
   }
   if (rc == DIRAC_OK) rc = finish_stats(S, (const char*)x, (const char*)b, P.tol);

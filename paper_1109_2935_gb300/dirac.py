@@ -24,7 +24,8 @@ ERR_NAMES = {0: "OK", -1: "ERR_ARG", -2: "ERR_CUDA", -3: "ERR_OOM", -4: "ERR_UNS
 WILSON_CLOVER, ASQTAD = 0, 1
 F64, F32, F16 = 0, 1, 2
 PARITY_FULL, PARITY_EVEN, PARITY_ODD = -1, 0, 1
-CG_NORMAL, CG_EVEN_NORMAL, BICGSTAB, GCR_DD, GCR, BICGSTAB_EO, GCR_EO = 0, 1, 2, 3, 4, 5, 6
+CG_NORMAL, CG_EVEN_NORMAL, BICGSTAB, GCR_DD, GCR, BICGSTAB_EO, GCR_EO, GCR_PTC = 0, 1, 2, 3, 4, 5, 6, 7
+PRECOND_NAMES = {0: "none", 1: "schwarz", 2: "ptc"}
 
 
 class DiracParams(ctypes.Structure):
@@ -44,10 +45,24 @@ class SolverStats(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("restarts", ctypes.c_int),
                 ("reliable_updates", ctypes.c_int), ("dslash_calls", ctypes.c_int),
                 ("precond_calls", ctypes.c_int), ("true_rel_resid", ctypes.c_double),
-                ("seconds", ctypes.c_double), ("flops", ctypes.c_double)]
+                ("seconds", ctypes.c_double), ("flops", ctypes.c_double),
+                ("precond_kind", ctypes.c_int), ("precond_reduction", ctypes.c_double * 2)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        d = {k: getattr(self, k) for k, _ in self._fields_}
+        d["precond_reduction"] = list(self.precond_reduction)
+        d["precond"] = PRECOND_NAMES.get(self.precond_kind, self.precond_kind)
+        return d
+
+
+class PtcParams(ctypes.Structure):
+    _fields_ = [("layers", ctypes.c_int), ("channels", ctypes.c_int * 5)]
+
+
+class PtcTrainParams(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_int), ("batch", ctypes.c_int), ("lr", ctypes.c_double),
+                ("beta1", ctypes.c_double), ("beta2", ctypes.c_double), ("eps", ctypes.c_double),
+                ("seed", ctypes.c_uint)]
 
 
 if not os.path.exists(LIB_PATH):
@@ -87,6 +102,16 @@ _SIGS = {
                                  ctypes.c_char_p, _sz]),
     "solve_multishift": (_ci, [_vp, ctypes.POINTER(_vp), _vp, ctypes.POINTER(ctypes.c_double), _ci,
                                ctypes.POINTER(SolverParams), ctypes.POINTER(SolverStats), _vp]),
+    "dirac_ptc_create": (_ci, [_vp, ctypes.POINTER(PtcParams), ctypes.POINTER(_vp)]),
+    "dirac_ptc_num_weights": (ctypes.c_longlong, [_vp]),
+    "dirac_ptc_set_weights": (_ci, [_vp, _pd, ctypes.c_longlong]),
+    "dirac_ptc_get_weights": (_ci, [_vp, _pd, ctypes.c_longlong]),
+    "dirac_ptc_apply": (_ci, [_vp, _vp, _vp, _vp]),
+    "dirac_ptc_gradient": (_ci, [_vp, _vp, _vp, _pd, _pd, _vp]),
+    "dirac_ptc_train": (_ci, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), _ci,
+                              ctypes.POINTER(PtcTrainParams), _pd, _vp]),
+    "dirac_ptc_attach": (_ci, [_vp, _vp, _ci]),
+    "dirac_ptc_destroy": (_ci, [_vp]),
 }
 EXPORTED = tuple(_SIGS)
 for _name, (_res, _args) in _SIGS.items():
@@ -327,3 +352,84 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+class Ptc:
+    """A gauge-equivariant parallel-transport convolution network on a Wilson-clover
+    lattice (dirac_ptc_*): K = L_n ... L_1 with channels (1, c_1, ..., 1). Weights are
+    exchanged as a list of complex arrays shaped (9, c_out, c_in, 4, 4) per layer;
+    fields are FP32 full fields in the library layout (``Lattice.to_device(.., F32)``)."""
+
+    def __init__(self, lattice, channels=(1, 2, 1)):
+        self.lat = lattice
+        self.channels = tuple(channels)
+        p = PtcParams()
+        p.layers = len(channels) - 1
+        p.channels[:len(channels)] = list(channels)
+        h = _vp()
+        lattice.check(dirac_ptc_create(lattice.ctx, ctypes.byref(p), ctypes.byref(h)), "dirac_ptc_create")
+        self.net = h
+        self.shapes = [(9, channels[l + 1], channels[l], 4, 4) for l in range(len(channels) - 1)]
+        self.n = dirac_ptc_num_weights(self.net)
+
+    def set_weights(self, ws):
+        import numpy as np
+        flat = np.concatenate([np.asarray(w, dtype=np.complex128).reshape(-1) for w in ws])
+        if flat.size != self.n:
+            raise ValueError(f"expected {self.n} complex weights, got {flat.size}")
+        buf = np.ascontiguousarray(flat).view(np.float64)
+        self.lat.check(dirac_ptc_set_weights(self.net, buf.ctypes.data_as(_pd), self.n),
+                       "dirac_ptc_set_weights")
+
+    def _split(self, flat):
+        out, off = [], 0
+        for s in self.shapes:
+            k = s[0] * s[1] * s[2] * s[3] * s[4]
+            out.append(flat[off:off + k].reshape(s))
+            off += k
+        return out
+
+    def get_weights(self):
+        import numpy as np
+        buf = np.zeros(2 * self.n)
+        self.lat.check(dirac_ptc_get_weights(self.net, buf.ctypes.data_as(_pd), self.n),
+                       "dirac_ptc_get_weights")
+        return self._split(buf.view(np.complex128))
+
+    def apply(self, out, inp, stream=None):
+        return self.lat.check(dirac_ptc_apply(self.net, out.data_ptr(), inp.data_ptr(), _stream(stream)),
+                              "dirac_ptc_apply")
+
+    def gradient(self, r, v, stream=None):
+        """(loss, [dL/dconj(W_l)]) of one pair, L = |K r - v|^2 / |v|^2."""
+        import numpy as np
+        loss = ctypes.c_double()
+        buf = np.zeros(2 * self.n)
+        self.lat.check(dirac_ptc_gradient(self.net, r.data_ptr(), v.data_ptr(), ctypes.byref(loss),
+                                          buf.ctypes.data_as(_pd), _stream(stream)), "dirac_ptc_gradient")
+        return loss.value, self._split(buf.view(np.complex128))
+
+    def train(self, vs, rs=None, steps=100, batch=4, lr=1e-2, beta1=0.9, beta2=0.999, eps=1e-8,
+              seed=0, stream=None):
+        """Adam on the pairs (r_i, v_i) (r_i = M v_i computed by the library when rs is
+        None). Returns the batch loss before each step."""
+        import numpy as np
+        n = len(vs)
+        vp = (_vp * n)(*[v.data_ptr() for v in vs])
+        rp = (_vp * n)(*[r.data_ptr() for r in rs]) if rs is not None else None
+        P = PtcTrainParams(steps, batch, lr, beta1, beta2, eps, seed)
+        loss = np.zeros(max(steps, 1))
+        self.lat.check(dirac_ptc_train(self.net, rp, vp, n, ctypes.byref(P), loss.ctypes.data_as(_pd),
+                                       _stream(stream)), "dirac_ptc_train")
+        return loss[:steps]
+
+    def attach(self, force=False):
+        return self.lat.check(dirac_ptc_attach(self.lat.ctx, self.net, int(force)), "dirac_ptc_attach")
+
+    def detach(self):
+        return self.lat.check(dirac_ptc_attach(self.lat.ctx, None, 0), "dirac_ptc_attach")
+
+    def close(self):
+        if self.net and self.lat.ctx:
+            dirac_ptc_destroy(self.net)
+        self.net = None

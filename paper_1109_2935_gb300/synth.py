@@ -159,3 +159,18 @@ def gauge_transform(U, G, hop=1):
     for mu in range(4):
         out[..., mu, :, :] = G @ U[..., mu, :, :] @ _roll(G, mu, hop).conj().transpose(-1, -2)
     return out
+
+
+def ptc_weights(channels, seed, noise=0.05):
+    """Initial weights of a parallel-transport convolution network with the given
+    channel list: each layer passes channel 0 through on the local path (identity spin
+    matrix) plus complex Gaussian entries of standard deviation `noise` everywhere, so no
+    hidden channel starts dead. Complex128 tensors shaped (9, c_out, c_in, 4, 4)."""
+    g = _gen(seed, "cpu")
+    out = []
+    for l in range(len(channels) - 1):
+        shape = (9, channels[l + 1], channels[l], 4, 4)
+        W = _cgauss(shape, g, "cpu", noise)
+        W[0, 0, 0] += torch.eye(4, dtype=W.dtype)
+        out.append(W)
+    return out

@@ -45,7 +45,8 @@ def test_struct_layouts_match_header(tmp_path):
     build.build()
     from paper_1109_2935_gb300 import dirac
     structs = {"dirac_params": dirac.DiracParams, "dirac_solver_params": dirac.SolverParams,
-               "dirac_solver_stats": dirac.SolverStats}
+               "dirac_solver_stats": dirac.SolverStats, "dirac_ptc_params": dirac.PtcParams,
+               "dirac_ptc_train_params": dirac.PtcTrainParams}
     cc = shutil.which("gcc") or shutil.which("cc")
     if cc is None:
         import pytest

@@ -39,15 +39,15 @@ def test_gauge_equivariance():
     Ut = synth.gauge_transform(torch.from_numpy(U), G).numpy()
     G = G.numpy()
     Gr = np.einsum("...ab,...sb->...sa", G, r)
-    lhs, _ = ptc.net_forward(Ut, W1, W2, Gr)
-    rhs = np.einsum("...ab,...sb->...sa", G, ptc.net_forward(U, W1, W2, r)[0])
+    lhs, _ = ptc.net_forward(Ut, [W1, W2], Gr)
+    rhs = np.einsum("...ab,...sb->...sa", G, ptc.net_forward(U, [W1, W2], r)[0])
     assert np.max(np.abs(lhs - rhs)) < 1e-12
 
 
 def test_identity_network():
     dims = (2, 2, 2, 4)
     U, r, _ = _fields(dims)
-    k, _ = ptc.net_forward(U, ptc.identity_weights(2, 1, 2.0), ptc.identity_weights(1, 2, 0.5), r)
+    k, _ = ptc.net_forward(U, [ptc.identity_weights(2, 1, 2.0), ptc.identity_weights(1, 2, 0.5)], r)
     assert np.max(np.abs(k - r)) < 1e-15
 
 
@@ -57,18 +57,18 @@ def test_weight_gradient_finite_differences():
     U, r, v = _fields(dims, 11)
     rng = np.random.default_rng(1)
     W1, W2 = _rand_w(rng, 2, 1), _rand_w(rng, 1, 2)
-    L, g1, g2 = ptc.loss_and_grad(U, W1, W2, r, v)
+    L, (g1, g2) = ptc.loss_and_grad(U, [W1, W2], r, v)
     eps = 1e-6
     for which, W, g in ((1, W1, g1), (2, W2, g2)):
         for trial in range(4):
             dW = _rand_w(rng, W.shape[1], W.shape[2], 1.0)
             Wp, Wm = W + eps * dW, W - eps * dW
             if which == 1:
-                Lp = ptc.loss_and_grad(U, Wp, W2, r, v)[0]
-                Lm = ptc.loss_and_grad(U, Wm, W2, r, v)[0]
+                Lp = ptc.loss_and_grad(U, [Wp, W2], r, v)[0]
+                Lm = ptc.loss_and_grad(U, [Wm, W2], r, v)[0]
             else:
-                Lp = ptc.loss_and_grad(U, W1, Wp, r, v)[0]
-                Lm = ptc.loss_and_grad(U, W1, Wm, r, v)[0]
+                Lp = ptc.loss_and_grad(U, [W1, Wp], r, v)[0]
+                Lm = ptc.loss_and_grad(U, [W1, Wm], r, v)[0]
             fd = (Lp - Lm) / (2 * eps)
             an = 2 * np.real(np.vdot(g, dW))
             assert abs(fd - an) <= 1e-6 * max(1.0, abs(an)), (which, fd, an)
@@ -103,8 +103,27 @@ def test_training_by_adam_reduces_loss():
     m1, v1, m2, v2 = (np.zeros_like(W1), np.zeros_like(W1), np.zeros_like(W2), np.zeros_like(W2))
     L0 = None
     for t in range(1, 16):
-        L, g1, g2 = ptc.loss_and_grad(U, W1, W2, r, v)
+        L, (g1, g2) = ptc.loss_and_grad(U, [W1, W2], r, v)
         L0 = L if L0 is None else L0
         W1, m1, v1 = ptc.adam_step(W1, g1, m1, v1, t, 0.02)
         W2, m2, v2 = ptc.adam_step(W2, g2, m2, v2, t, 0.02)
-    assert ptc.loss_and_grad(U, W1, W2, r, v)[0] < 0.7 * L0
+    assert ptc.loss_and_grad(U, [W1, W2], r, v)[0] < 0.7 * L0
+
+
+def test_three_layer_gradient_finite_differences():
+    """1 -> 2 -> 2 -> 1: the middle layer's gradient passes through two adjoint layers."""
+    dims = (2, 2, 2, 4)
+    U, r, v = _fields(dims, 13)
+    rng = np.random.default_rng(6)
+    Ws = [_rand_w(rng, 2, 1), _rand_w(rng, 2, 2), _rand_w(rng, 1, 2)]
+    L, grads = ptc.loss_and_grad(U, Ws, r, v)
+    eps = 1e-6
+    for l in range(3):
+        dW = _rand_w(rng, Ws[l].shape[1], Ws[l].shape[2], 1.0)
+        Wp = [w.copy() for w in Ws]
+        Wm = [w.copy() for w in Ws]
+        Wp[l] = Wp[l] + eps * dW
+        Wm[l] = Wm[l] - eps * dW
+        fd = (ptc.loss_and_grad(U, Wp, r, v)[0] - ptc.loss_and_grad(U, Wm, r, v)[0]) / (2 * eps)
+        an = 2 * np.real(np.vdot(grads[l], dW))
+        assert abs(fd - an) <= 1e-6 * max(1.0, abs(an)), (l, fd, an)
