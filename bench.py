@@ -212,6 +212,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer e2e timing")
     ap.add_argument("--no-asqtad", action="store_true", help="skip the asqtad rows")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched multi-RHS row")
+    ap.add_argument("--no-ptc", action="store_true", help="skip the learned-preconditioner row")
     ap.add_argument("--asqtad-dims", type=int, nargs=4, default=[48, 48, 48, 144],
                     help="asqtad lattice (48^3x144 unless profiling a smaller case)")
     ap.add_argument("--dims", type=int, nargs=4, default=list(DIMS),
@@ -319,6 +320,8 @@ def main():
     torch.cuda.empty_cache()
     if not args.no_batch:
         rows["batched_multi_rhs"] = measure_batch(dirac, synth, dev, stream, peak)
+    if not args.no_ptc and not args.no_solve:
+        rows["ptc_preconditioner"] = measure_ptc(dirac, synth, dev, stream)
     if not args.no_asqtad:
         ad = tuple(args.asqtad_dims)
         rows["asqtad_%dx%dx%dx%d" % ad] = measure_asqtad(dirac, synth, dev, stream, peak,
@@ -631,18 +634,116 @@ def _traffic_from_profile(dims):
     return int(t.group(1))
 
 
+PTC_DIMS, PTC_KAPPA, PTC_CHANNELS = (16, 16, 16, 16), 0.1355, (1, 4, 4, 1)
+PTC_STEPS, PTC_BATCH, PTC_LR = 400, 4, 1e-2
+
+
+def train_ptc(dirac, synth, dev, kappa):
+    """A PTC network trained on the 16^4 field (sigma 0.5, 3 smoothing steps, gauge seed
+    5001, source 5002) at `kappa`: pairs v = x* - x_k from GCR-DD iterates x_k of the
+    source (x* its 1e-10 solution) plus 8 Gaussian v, r = M v, Adam. Returns the lattice,
+    the network and a report."""
+    import torch
+    U = synth.wilson_gauge(PTC_DIMS, SIGMA, SMEAR, 5001, device=dev)
+    lat = dirac.Lattice(PTC_DIMS, dirac.WILSON_CLOVER, kappa=kappa, csw=CSW, block=BLOCK,
+                        mr_steps=MR_STEPS, recon=(18, 12, 12))
+    lat.load_gauge(U)
+    F64, F32, F16 = dirac.F64, dirac.F32, dirac.F16
+    b = lat.to_device(synth.wilson_spinor(PTC_DIMS, 5002).to(dev), F64)
+    xs = lat.new_field(F64)
+    t0 = time.time()
+    lat.solve(xs, b, dirac.GCR_DD, tol=1e-10, max_iter=4000, k_max=16, delta=0.1,
+              prec_sloppy=F32, prec_precond=F16, raise_on_error=False)
+    vs = []
+    for k in (2, 4, 8, 16, 32, 64, 128, 256):
+        xk = lat.new_field(F64)
+        lat.solve(xk, b, dirac.GCR_DD, tol=1e-10, max_iter=k, k_max=16, delta=0.1,
+                  prec_sloppy=F32, prec_precond=F16, raise_on_error=False)
+        lat.caxpy_norm(-1.0, xs, xk, F64)          # xk <- x_k - x*, the sign is irrelevant
+        v = lat.new_field(F32)
+        lat.convert(v, F32, xk, F64)
+        vs.append(v)
+    n_solver = len(vs)
+    for i in range(8):
+        vs.append(lat.to_device(synth.wilson_spinor(PTC_DIMS, 5100 + i).to(dev), F32))
+    make_s = time.time() - t0
+    net = dirac.Ptc(lat, PTC_CHANNELS)
+    net.set_weights([w.numpy() for w in synth.ptc_weights(PTC_CHANNELS, 5003)])
+    torch.cuda.synchronize()
+    t0 = time.time()
+    loss = net.train(vs, steps=PTC_STEPS, batch=PTC_BATCH, lr=PTC_LR, seed=1)
+    torch.cuda.synchronize()
+    ttrain = time.time() - t0
+    rep = {"lattice": "16x16x16x16", "kappa": kappa, "channels": list(PTC_CHANNELS),
+           "pairs": {"solver_iterates": n_solver, "gaussian": len(vs) - n_solver, "make_s": round(make_s, 3)},
+           "steps": PTC_STEPS, "batch": PTC_BATCH, "lr": PTC_LR, "seconds": round(ttrain, 4),
+           "ms_per_step": round(1e3 * ttrain / PTC_STEPS, 4),
+           "loss_first": round(float(loss[0]), 5), "loss_last10": round(float(loss[-10:].mean()), 5)}
+    return lat, net, vs, b, rep
+
+
+def _solve_row(lat, x, b, alg, sp, pp, budget):
+    st = lat.solve(x, b, alg, tol=1e-10, max_iter=budget, k_max=16, delta=0.1, prec_sloppy=sp,
+                   prec_precond=pp, raise_on_error=False)
+    return {k: (float(f"{v:.4g}") if isinstance(v, float) else v) for k, v in st.items()
+            if k in ("status", "iters", "restarts", "reliable_updates", "true_rel_resid", "seconds",
+                     "precond", "precond_reduction", "precond_calls", "dslash_calls")}
+
+
+def measure_ptc(dirac, synth, dev, stream):
+    """Learned PTC preconditioner on 16^4, kappa 0.1355, c_sw 1.0: training, the
+    network's application rate, and GCR with K = network / Schwarz / none against plain
+    FP64 GCR and FP64 GCR-DD, all to 1e-10."""
+    import torch
+    lat, net, vs, b, rep = train_ptc(dirac, synth, dev, PTC_KAPPA)
+    F64, F32, F16 = dirac.F64, dirac.F32, dirac.F16
+    out = {"workload": "16x16x16x16 csw=1.0 kappa=0.1355 sigma=0.5 smear=3", "train": rep}
+    fin, fout = vs[-1], lat.new_field(F32)
+    ms = _event_time(lambda: net.apply(fout, fin, stream=stream), 100, stream)
+    ch = PTC_CHANNELS
+    flops = sum(8 * min(ch[l], ch[l + 1]) * 264 + 9 * ch[l] * ch[l + 1] * 384 for l in range(len(ch) - 1))
+    V = PTC_DIMS[0] * PTC_DIMS[1] * PTC_DIMS[2] * PTC_DIMS[3]
+    out["apply"] = {"ms": round(ms, 4), "flop_per_site": flops,
+                    "TFLOPs": round(flops * V / (ms * 1e-3) / 1e12, 2),
+                    "frac_of_fp32_peak": round(flops * V / (ms * 1e-3) / 1e12 / FP32_PEAK_TFLOPS, 3)}
+    res = {}
+    runs = [("gcr_f64", dirac.GCR, F64, F64, None), ("gcr_dd_f64", dirac.GCR_DD, F64, F64, None),
+            ("gcr_mixed", dirac.GCR, F32, F32, None), ("gcr_dd_mixed", dirac.GCR_DD, F32, F16, None),
+            ("gcr_ptc_mixed", dirac.GCR_PTC, F32, F32, True),
+            ("gcr_ptc_select_mixed", dirac.GCR_PTC, F32, F16, False)]
+    for name, alg, sp, pp, force in runs:
+        if force is not None:
+            net.attach(force=force)
+        torch.cuda.synchronize()
+        res[name] = _solve_row(lat, lat.new_field(F64), b, alg, sp, pp, 4000)
+    for name in ("gcr_mixed", "gcr_dd_mixed", "gcr_ptc_mixed", "gcr_ptc_select_mixed"):
+        r = res[name]
+        for ref in ("gcr_f64", "gcr_dd_f64"):
+            if r["status"] == "OK" and res[ref]["status"] == "OK":
+                r[f"speedup_vs_{ref}"] = round(res[ref]["seconds"] / r["seconds"], 3)
+        if r["status"] == "OK" and res["gcr_dd_mixed"]["status"] == "OK":
+            r["iters_vs_gcr_dd_mixed"] = round(r["iters"] / res["gcr_dd_mixed"]["iters"], 3)
+            r["speedup_vs_gcr_dd_mixed"] = round(res["gcr_dd_mixed"]["seconds"] / r["seconds"], 3)
+    out["solves"] = res
+    net.close()
+    lat.close()
+    return out
+
+
 def run_solves(dirac, synth, U, src, dev):
     """Mixed-precision vs plain-FP64 solves on the same 24^3x128 field."""
     import torch
     out = {}
-    for kappa, tag, budget in ((KAPPA_SOLVE, "kappa_0.124", 4000), (KAPPA, "kappa_0.135", 600)):
+    for kappa, tag, budget, gcr_budget in ((KAPPA_SOLVE, "kappa_0.124", 4000, 1000),
+                                           (KAPPA, "kappa_0.135", 600, 2000)):
         lat = dirac.Lattice(DIMS, dirac.WILSON_CLOVER, kappa=kappa, csw=CSW, block=BLOCK,
                             mr_steps=MR_STEPS, recon=(18, 12, 12))
         lat.load_gauge(U)
         b = lat.to_device(src, dirac.F64)
         x = lat.new_field(dirac.F64)
         res = {}
-        runs = [("gcr_dd_mixed", dirac.GCR_DD, dirac.F16, dirac.F16, 0.1),
+        runs = [("gcr_f64", dirac.GCR, dirac.F64, dirac.F64, 0.0),
+                ("gcr_dd_mixed", dirac.GCR_DD, dirac.F16, dirac.F16, 0.1),
                 ("gcr_dd_f64", dirac.GCR_DD, dirac.F64, dirac.F64, 0.0),
                 ("bicgstab_mixed", dirac.BICGSTAB, dirac.F16, dirac.F16, 0.1),
                 ("bicgstab_f64", dirac.BICGSTAB, dirac.F64, dirac.F64, 0.0),
@@ -652,13 +753,27 @@ def run_solves(dirac, synth, U, src, dev):
             if kappa == KAPPA and name.endswith("f64"):
                 continue
             torch.cuda.synchronize()
-            st = lat.solve(x, b, alg, tol=1e-10, max_iter=budget if alg != dirac.GCR_DD else budget // 4,
+            st = lat.solve(x, b, alg, tol=1e-10, max_iter=budget if alg not in (dirac.GCR_DD, dirac.GCR) else gcr_budget,
                            k_max=16, delta=delta, prec_sloppy=sp, prec_precond=pp, raise_on_error=False)
             res[name] = {k: (float(f"{v:.4g}") if isinstance(v, float) else v) for k, v in st.items()}
-        for alg in ("gcr_dd", "bicgstab", "bicgstab_eo"):
-            a, b_ = res.get(f"{alg}_mixed"), res.get(f"{alg}_f64")
+        # learned preconditioner: weights trained on the 16^4 field at the same kappa
+        plat, pnet, _, _, rep = train_ptc(dirac, synth, dev, kappa)
+        w = pnet.get_weights()
+        plat.close()
+        net = dirac.Ptc(lat, PTC_CHANNELS)
+        net.set_weights(w)
+        for name, force, pp in (("gcr_ptc_mixed", True, dirac.F32), ("gcr_ptc_select_mixed", False, dirac.F16)):
+            net.attach(force=force)
+            torch.cuda.synchronize()
+            res[name] = _solve_row(lat, x, b, dirac.GCR_PTC, dirac.F32, pp, gcr_budget)
+            res[name]["trained_on"] = rep
+        for alg in ("gcr_dd", "bicgstab", "bicgstab_eo", "gcr_ptc", "gcr_ptc_select"):
+            a, b_ = res.get(f"{alg}_mixed"), res.get(f"{alg}_f64") or res.get("gcr_dd_f64")
             if a and b_ and a["status"] == "OK" and b_["status"] == "OK":
                 res[f"{alg}_speedup_vs_f64"] = round(b_["seconds"] / a["seconds"], 3)
+            g = res.get("gcr_f64")
+            if a and g and a["status"] == "OK" and g["status"] == "OK":
+                res[f"{alg}_speedup_vs_plain_gcr_f64"] = round(g["seconds"] / a["seconds"], 3)
         out[tag] = res
         lat.close()
     return out
