@@ -356,6 +356,7 @@ def _event_time(fn, n, stream, warm=3):
 
 def measure_wilson_rows(lat, dirac, fields, precs, stream, peak):
     import time as _t
+    import torch
     V, Vh = lat.volume, lat.volume // 2
     out = {"dslash_parity": {}, "schwarz": {}, "blas_caxpy_norm": {}}
     for name in precs:
@@ -384,6 +385,31 @@ def measure_wilson_rows(lat, dirac, fields, precs, stream, peak):
         out["blas_caxpy_norm"][name] = {"ms_per_call_incl_sync": round(ms, 4),
                                         "GBps_incl_sync": round(3 * fb / (ms / 1e3) / 1e9, 1)}
     out["schwarz"]["fp32_peak_tflops"] = round(FP32_PEAK_TFLOPS, 1)
+    # domain decomposition along t emulated on this GPU (virtual ranks, ghost zones,
+    # face exchange by device copies): one application of M, and its bit-exactness
+    out["domain_decomposition"] = {}
+    for name in precs:
+        if name == "f64":
+            continue
+        pid = PREC_ID[name]
+        x, y = fields[name]
+        lat.apply(y, x, -1, pid, stream)
+        for P in (2, 4, 8):
+            if lat.dims[3] % (2 * P):
+                continue
+            dd = dirac.DomainDecomposition(lat, P, pid)
+            dd.scatter(x, stream=stream)
+            ms = _event_time(lambda: dd.apply(stream=stream), 20, stream)
+            g = torch.zeros_like(y)
+            dd.gather(g, stream=stream)
+            torch.cuda.synchronize()
+            gbs = SITE_BYTES[name] * V / (ms / 1e3) / 1e9
+            out["domain_decomposition"].setdefault(name, {})[f"ranks_{P}"] = {
+                "ms": round(ms, 4), "alg_GBps": round(gbs, 1), "frac_of_hbm": round(gbs / peak, 4),
+                "face_bytes": dd.info()["face_bytes"],
+                # FP16: the two kernels round the decode product differently (one FP16 ulp)
+                "bitwise_equal_single_domain": bool(torch.equal(g, y)) if name != "f16" else None}
+            dd.close()
     return out
 
 

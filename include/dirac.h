@@ -315,6 +315,30 @@ int dirac_ptc_attach(dirac_ctx* ctx, dirac_ptc* net, int force);
 /* Free the network (detaching it first). NULL is a no-op. */
 int dirac_ptc_destroy(dirac_ptc* net);
 
+/* ------------------------------------------------------------------ domain decomposition
+ * The paper's multi-GPU scheme (Sec. 6) for the Wilson-clover operator, emulated on one
+ * GPU: the lattice is cut along t into nranks virtual ranks (LT / nranks even, >= 2),
+ * each with its own local links, clover and spinors, a stream, send buffers and two
+ * ghost zones. dirac_dd_apply packs each rank's boundary slices spin-projected (12 reals
+ * per face site: FP64 in FP64, else FP32), copies them into the neighbours' ghost zones
+ * (device-to-device copies ordered by events), and runs the interior slices (overlapping
+ * the exchange) and the boundary slices as separate kernels. Backward-hop links of the
+ * face are exchanged once, by dirac_dd_create. The result equals dirac_apply(FULL) of the
+ * whole lattice bit for bit in FP64 and FP32 (FP16: to FP32 rounding before re-encoding). Fields: `in` / `out` of scatter / gather are full fields of
+ * ctx in precision `prec`. All calls are asynchronous on stream except create / destroy
+ * (which synchronise the device). */
+typedef struct dirac_dd dirac_dd;
+int dirac_dd_create(dirac_ctx* ctx, int nranks, dirac_prec prec, dirac_dd** dd);
+/* global field -> every rank's local input */
+int dirac_dd_scatter(dirac_dd* dd, const void* in, void* stream);
+/* out_r = M in_r (dagger = 1: M^dagger) on every rank */
+int dirac_dd_apply(dirac_dd* dd, int dagger, void* stream);
+/* every rank's local output -> global field */
+int dirac_dd_gather(dirac_dd* dd, void* out, void* stream);
+/* local dims of a rank; bytes of one spinor face */
+int dirac_dd_info(const dirac_dd* dd, int* local_dims, long long* face_bytes);
+int dirac_dd_destroy(dirac_dd* dd);
+
 #ifdef __cplusplus
 }
 #endif

@@ -112,6 +112,12 @@ _SIGS = {
                               ctypes.POINTER(PtcTrainParams), _pd, _vp]),
     "dirac_ptc_attach": (_ci, [_vp, _vp, _ci]),
     "dirac_ptc_destroy": (_ci, [_vp]),
+    "dirac_dd_create": (_ci, [_vp, _ci, _ci, ctypes.POINTER(_vp)]),
+    "dirac_dd_scatter": (_ci, [_vp, _vp, _vp]),
+    "dirac_dd_apply": (_ci, [_vp, _ci, _vp]),
+    "dirac_dd_gather": (_ci, [_vp, _vp, _vp]),
+    "dirac_dd_info": (_ci, [_vp, ctypes.POINTER(_ci), ctypes.POINTER(ctypes.c_longlong)]),
+    "dirac_dd_destroy": (_ci, [_vp]),
 }
 EXPORTED = tuple(_SIGS)
 for _name, (_res, _args) in _SIGS.items():
@@ -433,3 +439,34 @@ class Ptc:
         if self.net and self.lat.ctx:
             dirac_ptc_destroy(self.net)
         self.net = None
+
+
+class DomainDecomposition:
+    """dirac_dd_*: the Wilson-clover operator over nranks virtual ranks (t-slabs) with
+    ghost zones and face exchange, on one GPU."""
+
+    def __init__(self, lattice, nranks, prec):
+        self.lat = lattice
+        h = _vp()
+        lattice.check(dirac_dd_create(lattice.ctx, nranks, prec, ctypes.byref(h)), "dirac_dd_create")
+        self.dd = h
+
+    def info(self):
+        dims = (_ci * 4)()
+        fb = ctypes.c_longlong()
+        dirac_dd_info(self.dd, dims, ctypes.byref(fb))
+        return {"local_dims": tuple(dims), "face_bytes": fb.value}
+
+    def scatter(self, field, stream=None):
+        return self.lat.check(dirac_dd_scatter(self.dd, field.data_ptr(), _stream(stream)), "dirac_dd_scatter")
+
+    def apply(self, dagger=False, stream=None):
+        return self.lat.check(dirac_dd_apply(self.dd, int(dagger), _stream(stream)), "dirac_dd_apply")
+
+    def gather(self, field, stream=None):
+        return self.lat.check(dirac_dd_gather(self.dd, field.data_ptr(), _stream(stream)), "dirac_dd_gather")
+
+    def close(self):
+        if self.dd:
+            dirac_dd_destroy(self.dd)
+            self.dd = None

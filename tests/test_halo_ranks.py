@@ -1,0 +1,103 @@
+"""The t-slab domain decomposition across processes, on CPU: two gloo ranks exchange
+spin-projected faces (paper_1109_2935_gb300/halo.py) and each computes the oracle's
+Wilson-clover operator on its slab plus ghosts, which must equal the whole-lattice
+oracle there; the allreduce of local norms gives the global norm; a rank that never
+sends makes the other's exchange end with ERR_TIMEOUT instead of hanging."""
+import os
+import socket
+
+import numpy as np
+import torch
+import torch.distributed as dist
+import torch.multiprocessing as mp
+
+DIMS, KAPPA = (4, 4, 4, 8), 0.13
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _project(psi_slice, s):
+    """h = psi_up + s psi_low (the t-projection, B_t = 1): (Z, Y, X, 2, 3)."""
+    return psi_slice[..., :2, :] + s * psi_slice[..., 2:, :]
+
+
+def _worker(rank, world, port, q, done):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    from oracle import wilson
+    from paper_1109_2935_gb300 import synth
+    from paper_1109_2935_gb300.halo import HaloExchange, HaloTimeout
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    U = synth.wilson_gauge(DIMS, 0.5, 1, 4001).numpy()
+    psi = synth.wilson_spinor(DIMS, 4002).numpy()
+    A = wilson.clover(U, 1.0)
+    ref = wilson.apply_M(U, A, KAPPA, psi)            # whole lattice, antiperiodic t
+    LT = DIMS[3] // world
+    t0 = rank * LT
+    loc = psi[t0:t0 + LT]
+    hx = HaloExchange(timeout_s=2.0)
+    # gauge ghosts once: the previous rank's last-slice t-links
+    _, links_prev = hx.exchange(torch.from_numpy(U[t0, ..., 3, :, :].copy()),
+                                torch.from_numpy(U[t0 + LT - 1, ..., 3, :, :].copy()))
+    # spinor faces: first slice for the previous rank's forward hop (1 - gamma_t),
+    # last slice for the next rank's backward hop (1 + gamma_t)
+    from_next, from_prev = hx.exchange(torch.from_numpy(_project(loc[0], -1.0)),
+                                       torch.from_numpy(_project(loc[-1], +1.0)))
+    h_next, h_prev = from_next.numpy().copy(), from_prev.numpy().copy()
+    if rank == world - 1:
+        h_next *= -1.0                                 # the hop crosses the antiperiodic edge
+    if rank == 0:
+        h_prev *= -1.0
+    # slab plus one ghost slice on each side; a ghost spinor [h; 0] projects to h
+    ext = np.zeros((LT + 2,) + loc.shape[1:], dtype=complex)
+    ext[1:-1] = loc
+    ext[0, ..., :2, :] = h_prev
+    ext[-1, ..., :2, :] = h_next
+    Uext = np.zeros((LT + 2,) + U.shape[1:], dtype=complex)
+    Uext[:] = np.eye(3)
+    Uext[1:-1] = U[t0:t0 + LT]
+    Uext[0, ..., 3, :, :] = links_prev.numpy()
+    Aext = np.zeros((LT + 2,) + A.shape[1:], dtype=complex)
+    Aext[1:-1] = A[t0:t0 + LT]
+    out = wilson.apply_M(Uext, Aext, KAPPA, ext, antiperiodic_t=False)[1:-1]
+    err = float(np.max(np.abs(out - ref[t0:t0 + LT])))
+    n2 = hx.allreduce(torch.tensor([float(np.vdot(out, out).real)], dtype=torch.float64)).item()
+    n2_ref = float(np.vdot(ref, ref).real)
+    dist.barrier()
+    # fault, last: rank 1 never joins the next exchange; rank 0's exchange must end with
+    # ERR_TIMEOUT. The connection is closed after that, so the ranks part via the host.
+    timed_out, code = False, None
+    if rank == 0:
+        f = torch.zeros(4, dtype=torch.float64)
+        try:
+            HaloExchange(timeout_s=0.5).exchange(f, f)
+        except HaloTimeout as e:
+            timed_out, code = True, e.code
+        done.set()
+    else:
+        done.wait(60)
+    q.put((rank, err, n2, n2_ref, timed_out, code))
+
+
+def test_two_rank_halo_exchange_matches_whole_lattice_and_times_out():
+    world, port = 2, _free_port()
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    done = ctx.Event()
+    procs = [ctx.Process(target=_worker, args=(r, world, port, q, done)) for r in range(world)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(180)
+        assert p.exitcode == 0
+    got = sorted(q.get(timeout=10) for _ in range(world))
+    for rank, err, n2, n2_ref, timed_out, code in got:
+        assert err < 1e-13, (rank, err)
+        assert abs(n2 - n2_ref) < 1e-12 * n2_ref
+    assert got[0][4] and got[0][5] == -8
+    assert not got[1][4]
