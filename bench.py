@@ -708,6 +708,28 @@ def train_ptc(dirac, synth, dev, kappa):
     return lat, net, vs, b, rep
 
 
+def ptc_apply_rates(lat, net, fin, stream, dims):
+    """One application of the network: tensor-core (BF16 operands, FP32 accumulation)
+    and FP32 CUDA-core layers, nominal flops per site of the layer arithmetic."""
+    ch = PTC_CHANNELS
+    flops = sum(8 * min(ch[l], ch[l + 1]) * 264 + 9 * ch[l] * ch[l + 1] * 384 for l in range(len(ch) - 1))
+    V = dims[0] * dims[1] * dims[2] * dims[3]
+    fout = fin.clone()
+    out = {"flop_per_site": flops}
+    for name, on in (("tensor_cores", True), ("fp32", False)):
+        net.tensor_cores(on)
+        ms = _event_time(lambda: net.apply(fout, fin, stream=stream), 50, stream)
+        tf = flops * V / (ms * 1e-3) / 1e12
+        out[name] = {"ms": round(ms, 4), "TFLOPs_nominal": round(tf, 2)}
+    out["fp32"]["frac_of_fp32_peak"] = round(out["fp32"]["TFLOPs_nominal"] / FP32_PEAK_TFLOPS, 3)
+    out["speedup_tensor_cores"] = round(out["fp32"]["ms"] / out["tensor_cores"]["ms"], 3)
+    # the solves that follow use the faster path on this lattice
+    fast = out["tensor_cores"]["ms"] < out["fp32"]["ms"]
+    net.tensor_cores(fast)
+    out["solver_uses"] = "tensor_cores" if fast else "fp32"
+    return out
+
+
 def _solve_row(lat, x, b, alg, sp, pp, budget):
     st = lat.solve(x, b, alg, tol=1e-10, max_iter=budget, k_max=16, delta=0.1, prec_sloppy=sp,
                    prec_precond=pp, raise_on_error=False)
@@ -724,14 +746,7 @@ def measure_ptc(dirac, synth, dev, stream):
     lat, net, vs, b, rep = train_ptc(dirac, synth, dev, PTC_KAPPA)
     F64, F32, F16 = dirac.F64, dirac.F32, dirac.F16
     out = {"workload": "16x16x16x16 csw=1.0 kappa=0.1355 sigma=0.5 smear=3", "train": rep}
-    fin, fout = vs[-1], lat.new_field(F32)
-    ms = _event_time(lambda: net.apply(fout, fin, stream=stream), 100, stream)
-    ch = PTC_CHANNELS
-    flops = sum(8 * min(ch[l], ch[l + 1]) * 264 + 9 * ch[l] * ch[l + 1] * 384 for l in range(len(ch) - 1))
-    V = PTC_DIMS[0] * PTC_DIMS[1] * PTC_DIMS[2] * PTC_DIMS[3]
-    out["apply"] = {"ms": round(ms, 4), "flop_per_site": flops,
-                    "TFLOPs": round(flops * V / (ms * 1e-3) / 1e12, 2),
-                    "frac_of_fp32_peak": round(flops * V / (ms * 1e-3) / 1e12 / FP32_PEAK_TFLOPS, 3)}
+    out["apply"] = ptc_apply_rates(lat, net, vs[-1], stream, PTC_DIMS)
     res = {}
     runs = [("gcr_f64", dirac.GCR, F64, F64, None), ("gcr_dd_f64", dirac.GCR_DD, F64, F64, None),
             ("gcr_mixed", dirac.GCR, F32, F32, None), ("gcr_dd_mixed", dirac.GCR_DD, F32, F16, None),
@@ -788,6 +803,8 @@ def run_solves(dirac, synth, U, src, dev):
         plat.close()
         net = dirac.Ptc(lat, PTC_CHANNELS)
         net.set_weights(w)
+        res["ptc_apply"] = ptc_apply_rates(lat, net, lat.to_device(src, dirac.F32), torch.cuda.current_stream(),
+                                           DIMS)
         for name, force, pp in (("gcr_ptc_mixed", True, dirac.F32), ("gcr_ptc_select_mixed", False, dirac.F16)):
             net.attach(force=force)
             torch.cuda.synchronize()

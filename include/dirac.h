@@ -292,7 +292,8 @@ long long dirac_ptc_num_weights(const dirac_ptc* net);
 /* Copy n (= dirac_ptc_num_weights) complex weights from / to host memory, FP64 pairs. */
 int dirac_ptc_set_weights(dirac_ptc* net, const double* w, long long n);
 int dirac_ptc_get_weights(const dirac_ptc* net, double* w, long long n);
-/* out = K in (FP32 full fields, distinct; asynchronous on stream). */
+/* out = K in (FP32 full fields, distinct; asynchronous on stream; FP32 layers unless
+ * tensor cores are switched on by dirac_ptc_set_tensor_cores). */
 int dirac_ptc_apply(dirac_ptc* net, void* out, const void* in, void* stream);
 /* Loss L = ||K r - v||^2 / ||v||^2 of one pair and its derivative with respect to the
  * conjugate weights, dL/dconj(W), into grad (host, FP64 pairs, num_weights entries);
@@ -306,6 +307,11 @@ int dirac_ptc_gradient(dirac_ptc* net, const void* r, const void* v, double* los
  * Synchronises stream. */
 int dirac_ptc_train(dirac_ptc* net, const void* const* r, const void* const* v, int npairs,
                     const dirac_ptc_train_params* params, double* loss, void* stream);
+/* on = 1: dirac_ptc_apply and the GCR_PTC solver run every layer on the tensor cores
+ * (tcgen05, BF16 operands, FP32 accumulation: relative error ~1e-3, which the flexible
+ * outer GCR absorbs); on = 0 (default): the FP32 CUDA-core layers used for training. A
+ * tensor-core wait that gives up makes the next apply return DIRAC_ERR_TIMEOUT. */
+int dirac_ptc_set_tensor_cores(dirac_ptc* net, int on);
 /* Make net the preconditioner of DIRAC_SOLVER_GCR_PTC on ctx (NULL detaches). With
  * force = 0, every such solve starts by applying both the network and the Schwarz
  * preconditioner to the initial residual r0 and keeps the one with the smaller

@@ -142,6 +142,12 @@ int schur_reconstruct(dirac_ctx* c, char* x, const char* b, int prec, cudaStream
 int ptc_apply_internal(dirac_ptc* n, char* out, const char* in, cudaStream_t st);
 double ptc_flops_per_apply(const dirac_ptc* n);
 void ptc_release(dirac_ptc* n);
+// tensor-core inference layer (ptc_tc.cu): BF16 weight image of a layer, its size, and
+// one layer out[c] = sum W T in[c'] on FP32 full fields
+size_t ptc_tc_image_bytes(int cin, int cout);
+void ptc_tc_pack(int cin, int cout, const float2* w, void* img, cudaStream_t st);
+int ptc_tc_layer(int cin, int cout, int recon, const char* const* in, char* const* out, const char* gauge,
+                 const void* img, const Geom& g, int* err, cudaStream_t st);
 
 }  // namespace dirac
 

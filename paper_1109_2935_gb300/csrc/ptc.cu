@@ -433,6 +433,14 @@ struct dirac_ptc {
   double* dsc = nullptr;   // [0, MAXB): inv; [MAXB]: loss; then norm / loss partials
   char* hid = nullptr;     // inference: two hidden-layer buffers of MAXC fields
   size_t fb = 0;           // bytes of one FP32 full field
+  // tensor-core inference: BF16 weight images per layer, rebuilt after weight changes,
+  // and a host-mapped flag the kernels set when a wait gave up
+  int tc = 0;
+  char* tcimg = nullptr;
+  size_t tcoff[5] = {};
+  bool tc_dirty = true;
+  int* tc_err_h = nullptr;
+  int* tc_err_d = nullptr;
 };
 
 namespace dirac {
@@ -583,6 +591,32 @@ int forward_backward(dirac_ptc* n, const Work& W, const char* const* r, const ch
   return DIRAC_OK;
 }
 
+int ptc_apply_tc(dirac_ptc* n, char* out, const char* in, cudaStream_t st) {
+  if (*(volatile int*)n->tc_err_h) return net_err(n, DIRAC_ERR_TIMEOUT, "PTC tensor-core layer: a wait gave up");
+  if (!n->hid && cudaMalloc(&n->hid, 2 * MAXC * n->fb) != cudaSuccess) {
+    cudaGetLastError();
+    n->hid = nullptr;
+    return net_err(n, DIRAC_ERR_OOM, "PTC inference buffers");
+  }
+  if (n->tc_dirty) {
+    for (int l = 1; l <= n->L; ++l)
+      ptc_tc_pack(n->ch[l - 1], n->ch[l], reinterpret_cast<const float2*>(n->w) + n->woff[l - 1],
+                  n->tcimg + n->tcoff[l - 1], st);
+    n->tc_dirty = false;
+  }
+  for (int l = 1; l <= n->L; ++l) {
+    const char* a[MAXC];
+    char* b[MAXC];
+    for (int c = 0; c < n->ch[l - 1]; ++c)
+      a[c] = l == 1 ? in : n->hid + ((size_t)((l - 1) & 1) * MAXC + c) * n->fb;
+    for (int c = 0; c < n->ch[l]; ++c) b[c] = l == n->L ? out : n->hid + ((size_t)(l & 1) * MAXC + c) * n->fb;
+    int rc = ptc_tc_layer(n->ch[l - 1], n->ch[l], n->c->p.recon[P32], a, b, n->c->gauge[P32], n->tcimg + n->tcoff[l - 1],
+                          geom(n), n->tc_err_d, st);
+    if (rc) return net_err(n, rc, "PTC tensor-core layer launch");
+  }
+  return cuda_check(n->c, "PTC apply (tensor cores)");
+}
+
 double layer_flops(int cin, int cout) {
   // 8 transports of min(cin, cout) spinors (4 SU(3) matvecs, 66 flops each) and
   // 9 x cin x cout spin mixes (16 x 3 complex multiply-adds, 8 flops each)
@@ -596,6 +630,7 @@ int ptc_apply_internal(dirac_ptc* n, char* out, const char* in, cudaStream_t st)
   if (!n) return DIRAC_ERR_STATE;
   int rc = check_net(n);
   if (rc) return rc;
+  if (n->tc) return ptc_apply_tc(n, out, in, st);
   if (!n->hid) {
     if (cudaMalloc(&n->hid, 2 * MAXC * n->fb) != cudaSuccess) {
       cudaGetLastError();
@@ -633,6 +668,8 @@ void ptc_release(dirac_ptc* n) {
   cudaFree(n->partial);
   cudaFree(n->dsc);
   cudaFree(n->hid);
+  cudaFree(n->tcimg);
+  if (n->tc_err_h) cudaFreeHost(n->tc_err_h);
   delete n;
 }
 
@@ -676,11 +713,21 @@ extern "C" int dirac_ptc_create(dirac_ctx* c, const dirac_ptc_params* p, dirac_p
          cudaMemset(n->am, 0, nw * 8) == cudaSuccess && cudaMemset(n->av, 0, nw * 8) == cudaSuccess &&
          cudaMemset(n->grad, 0, nw * 16) == cudaSuccess;
   }
+  size_t img = 0;
+  for (int l = 1; l <= n->L; ++l) {
+    n->tcoff[l - 1] = img;
+    img += ptc_tc_image_bytes(n->ch[l - 1], n->ch[l]);
+  }
+  if (ok)
+    ok = cudaMalloc(&n->tcimg, img) == cudaSuccess &&
+         cudaHostAlloc(&n->tc_err_h, sizeof(int), cudaHostAllocMapped) == cudaSuccess &&
+         cudaHostGetDevicePointer(&n->tc_err_d, n->tc_err_h, 0) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
     ptc_release(n);
     return set_err(c, DIRAC_ERR_OOM, "PTC weights");
   }
+  *n->tc_err_h = 0;
   c->ptcs.push_back(n);
   *out = n;
   return DIRAC_OK;
@@ -695,6 +742,7 @@ extern "C" int dirac_ptc_set_weights(dirac_ptc* n, const double* w, long long cn
   for (long long i = 0; i < 2 * cnt; ++i) f[i] = (float)w[i];
   if (cudaMemcpy(n->w, f.data(), f.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess)
     return cuda_check(n->c, "PTC set weights");
+  n->tc_dirty = true;
   // new weights start a new optimisation
   cudaMemset(n->am, 0, f.size() * 4);
   cudaMemset(n->av, 0, f.size() * 4);
@@ -797,6 +845,7 @@ extern "C" int dirac_ptc_train(dirac_ptc* n, const void* const* r, const void* c
       vb[z] = (const char*)v[i];
     }
     if ((rc = forward_backward(n, W, rb, vb, true, st))) break;
+    n->tc_dirty = true;
     cudaMemcpyAsync(dloss + s, n->dsc + MAXB, sizeof(double), cudaMemcpyDeviceToDevice, st);
     n->t++;
     const double c1 = 1.0 - std::pow(P->beta1, (double)n->t), c2 = 1.0 - std::pow(P->beta2, (double)n->t);
@@ -813,6 +862,12 @@ extern "C" int dirac_ptc_train(dirac_ptc* n, const void* const* r, const void* c
   cudaFree(rbuf);
   if (rc == DIRAC_OK) rc = cuda_check(c, "PTC train");
   return rc;
+}
+
+extern "C" int dirac_ptc_set_tensor_cores(dirac_ptc* n, int on) {
+  if (!n || (on != 0 && on != 1)) return n ? net_err(n, DIRAC_ERR_ARG, "PTC: tensor cores on must be 0 or 1") : DIRAC_ERR_ARG;
+  n->tc = on;
+  return DIRAC_OK;
 }
 
 extern "C" int dirac_ptc_attach(dirac_ctx* c, dirac_ptc* n, int force) {

@@ -111,6 +111,7 @@ _SIGS = {
     "dirac_ptc_train": (_ci, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), _ci,
                               ctypes.POINTER(PtcTrainParams), _pd, _vp]),
     "dirac_ptc_attach": (_ci, [_vp, _vp, _ci]),
+    "dirac_ptc_set_tensor_cores": (_ci, [_vp, _ci]),
     "dirac_ptc_destroy": (_ci, [_vp]),
     "dirac_dd_create": (_ci, [_vp, _ci, _ci, ctypes.POINTER(_vp)]),
     "dirac_dd_scatter": (_ci, [_vp, _vp, _vp]),
@@ -428,6 +429,10 @@ class Ptc:
         self.lat.check(dirac_ptc_train(self.net, rp, vp, n, ctypes.byref(P), loss.ctypes.data_as(_pd),
                                        _stream(stream)), "dirac_ptc_train")
         return loss[:steps]
+
+    def tensor_cores(self, on=True):
+        """Inference on the tensor cores (BF16, FP32 accumulate) or the FP32 layers."""
+        return self.lat.check(dirac_ptc_set_tensor_cores(self.net, int(on)), "dirac_ptc_set_tensor_cores")
 
     def attach(self, force=False):
         return self.lat.check(dirac_ptc_attach(self.lat.ctx, self.net, int(force)), "dirac_ptc_attach")

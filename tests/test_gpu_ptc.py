@@ -42,6 +42,7 @@ def _rel(a, b):
 def test_forward_matches_oracle(dirac, dims, channels, recon):
     lat, U = _lattice(dirac, dims, recon=recon)
     net = dirac.Ptc(lat, channels)
+    net.tensor_cores(False)
     Ws = _weights(channels, 7)
     net.set_weights(Ws)
     # weights round to FP32 on the device; the oracle uses the same rounded values
@@ -113,6 +114,7 @@ def test_gauge_equivariance_full_size(dirac):
         lat = dirac.Lattice(dims, dirac.WILSON_CLOVER, kappa=0.1355, csw=1.0)
         lat.load_gauge(links)
         net = dirac.Ptc(lat, (1, 2, 1))
+        net.tensor_cores(False)
         net.set_weights(Ws)
         out = lat.new_field(F32)
         net.apply(out, lat.to_device(src.cuda(), F32))
@@ -125,6 +127,66 @@ def test_gauge_equivariance_full_size(dirac):
         lat.close()
     Gk = np.einsum("tzyxab,tzyxsb->tzyxsa", G.numpy(), outs[0])
     assert _rel(outs[1], Gk) < 1e-5
+
+
+@pytest.mark.parametrize("dims,channels,recon", [
+    ((4, 4, 4, 6), (1, 2, 1), (18, 18, 12)),
+    ((6, 6, 6, 10), (1, 4, 4, 1), (18, 12, 12)),     # 2160 sites: a ragged last tile of 128
+    ((4, 6, 4, 4), (1, 1), (18, 8, 12)),
+    ((4, 4, 4, 4), (1, 4, 2, 1), (18, 12, 12)),
+    ((2, 2, 2, 4), (1, 2, 4, 2, 1), (18, 18, 12)),
+    ((8, 8, 8, 8), (1, 4, 4, 1), (18, 12, 12)),
+])
+def test_tensor_core_forward_matches_oracle(dirac, dims, channels, recon):
+    """tcgen05 layers (BF16 operands, FP32 accumulation) against the FP64 oracle with the
+    device's FP32 weights: the error is the BF16 rounding of the transported inputs and
+    of the weights, ~2^-9 relative per operand."""
+    lat, U = _lattice(dirac, dims, recon=recon)
+    net = dirac.Ptc(lat, channels)
+    net.tensor_cores(True)
+    net.set_weights(_weights(channels, 17))
+    Wr = net.get_weights()
+    r = synth.wilson_spinor(dims, 19)
+    fin = lat.to_device(r.cuda(), F32)
+    out = lat.new_field(F32)
+    net.apply(out, fin)
+    got = lat.to_natural(out, F32, device="cpu").numpy()
+    rd = lat.to_natural(fin, F32, device="cpu").numpy()
+    expect, _ = optc.net_forward(U, Wr, rd)
+    assert _rel(got, expect) < 1e-2
+    site = np.linalg.norm((got - expect).reshape(-1, 12), axis=1) / np.linalg.norm(expect.reshape(-1, 12), axis=1)
+    assert np.max(site) < 5e-2
+    # switching back to the FP32 layers gives the 1e-5 result, and back again the same
+    # tensor-core result (the weight images are rebuilt only when weights change)
+    net.tensor_cores(False)
+    out32 = lat.new_field(F32)
+    net.apply(out32, fin)
+    assert _rel(lat.to_natural(out32, F32, device="cpu").numpy(), expect) < 1e-5
+    net.tensor_cores(True)
+    out2 = lat.new_field(F32)
+    net.apply(out2, fin)
+    assert torch.equal(out2, out)
+
+
+def test_tensor_core_weights_follow_training(dirac):
+    """After training steps change the weights, the tensor-core layers use the new ones."""
+    dims = (4, 4, 4, 8)
+    lat, U = _lattice(dirac, dims)
+    net = dirac.Ptc(lat, (1, 2, 1))
+    net.tensor_cores(True)
+    net.set_weights([w.numpy() for w in synth.ptc_weights((1, 2, 1), 3)])
+    r = lat.to_device(synth.wilson_spinor(dims, 23).cuda(), F32)
+    before = lat.new_field(F32)
+    net.apply(before, r)
+    vs = [lat.to_device(synth.wilson_spinor(dims, 30 + i).cuda(), F32) for i in range(4)]
+    net.train(vs, steps=5, batch=2, lr=1e-2)
+    after = lat.new_field(F32)
+    net.apply(after, r)
+    Wr = net.get_weights()
+    rd = lat.to_natural(r, F32, device="cpu").numpy()
+    expect, _ = optc.net_forward(U, Wr, rd)
+    assert not torch.equal(before, after)
+    assert _rel(lat.to_natural(after, F32, device="cpu").numpy(), expect) < 1e-2
 
 
 def test_one_adam_step_matches_oracle(dirac):
@@ -175,13 +237,16 @@ def _oracle_M(U, kappa):
     return lambda v: wilson.apply_M(U, A, kappa, v)
 
 
-def test_gcr_ptc_solve_reaches_1e10_and_beats_plain_gcr(dirac):
+@pytest.mark.parametrize("tensor_cores", [False, True])
+def test_gcr_ptc_solve_reaches_1e10_and_beats_plain_gcr(dirac, tensor_cores):
     """8^4, kappa 0.124: a trained network inside flexible GCR (forced) converges to 1e-10
-    (oracle true residual) in fewer iterations than GCR without a preconditioner."""
+    (oracle true residual) in fewer iterations than GCR without a preconditioner, with
+    the FP32 layers and with the tensor-core (BF16) layers."""
     dims = (8, 8, 8, 8)
     kappa = 0.124
     lat, U = _lattice(dirac, dims, kappa=kappa)
     net = dirac.Ptc(lat, (1, 2, 1))
+    net.tensor_cores(tensor_cores)
     net.set_weights([w.numpy() for w in synth.ptc_weights((1, 2, 1), 6)])
     vs = [lat.to_device(synth.wilson_spinor(dims, 700 + i).cuda(), F32) for i in range(8)]
     net.train(vs, steps=200, batch=4, lr=2e-2, seed=2)
