@@ -660,7 +660,7 @@ def _traffic_from_profile(dims):
     return int(t.group(1))
 
 
-PTC_DIMS, PTC_KAPPA, PTC_CHANNELS = (16, 16, 16, 16), 0.1355, (1, 4, 4, 1)
+PTC_DIMS, PTC_KAPPA, PTC_CHANNELS = (16, 16, 16, 16), 0.1355, (1, 2, 2, 1)
 PTC_STEPS, PTC_BATCH, PTC_LR = 400, 4, 1e-2
 
 
