@@ -265,6 +265,8 @@ int dirac_destroy(dirac_ctx* c) {
   fr(c->staging);
   fr(c->dscal);
   if (c->hmirror && cudaFreeHost(c->hmirror) != cudaSuccess) ok = false;
+  if (c->solve_stream && cudaStreamDestroy(c->solve_stream) != cudaSuccess) ok = false;
+  if (c->solve_event && cudaEventDestroy(c->solve_event) != cudaSuccess) ok = false;
   blas_destroy(c->blas);
   delete c;
   cudaGetLastError();  // leave no pending error behind for later contexts

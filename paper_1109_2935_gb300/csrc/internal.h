@@ -183,5 +183,9 @@ struct dirac_ctx {
   std::vector<dirac_ptc*> ptcs;
   dirac_ptc* ptc_attached = nullptr;
   int ptc_force = 0;
+  // solve(): private stream (graph capture needs a non-default stream) and the event that
+  // orders it after the caller's stream
+  cudaStream_t solve_stream = nullptr;
+  cudaEvent_t solve_event = nullptr;
   std::string err;
 };

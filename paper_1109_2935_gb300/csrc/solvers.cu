@@ -255,6 +255,7 @@ struct Ctx {
   double* mirror = nullptr;   // device alias of the mapped host mirror
   volatile double* hmirror = nullptr;
   cudaEvent_t ev[2] = {nullptr, nullptr};
+  bool graphs = false;        // GCR: replay captured steps (needs a capturable stream)
 
   char* get(int prec) {
     size_t bytes = (parity < 0 ? 2 : 1) * spinor_half_bytes(prec, c->nr, c->Vh);
@@ -552,8 +553,11 @@ int solve_gcr(Ctx& S, char* x, const char* b, const dirac_solver_params& P, int 
   S.stats->precond_kind = kind;
   KC((k_init<<<1, 1, 0, S.st>>>(S.S)));
   auto gb = [&](int i, int k) { return S.slot(S_GB + 4 * (i * KMAX + k) + 1); };
-  int k = 0;
-  while (r0n2 > target && S.stats->iters < P.max_iter) {
+  // One GCR step at Krylov index k: p_k = K r_k, z_k = M p_k, orthogonalisation, the
+  // residual update. Its launches depend only on k, so from the second restart cycle on
+  // each step replays a CUDA graph captured the cycle before (fewer host launches;
+  // statistics are added as the captured step counted them).
+  auto step = [&](int k) -> int {
     // p_k = K r_k
     if (kind != K_NONE) {
       TRY(precond_apply(S, K, kind, pv[k], rh, sp, pp));
@@ -582,6 +586,59 @@ int solve_gcr(Ctx& S, char* x, const char* b, const dirac_solver_params& P, int 
     BT(blas_caxpy_norm(B, cptr(S.slot(S_GA + 4 * k), -1), S.f(zv[k], sp), S.f(rh, sp), nullptr, S.st,
                        S.slot(S_RH)));
     KC((k_mirror<<<1, 1, 0, S.st>>>(S.S, S_RH, S.mirror, k & 1, k)));
+    return DIRAC_OK;
+  };
+  struct Captured {
+    cudaGraphExec_t exec = nullptr;
+    int state = 0;  // 0: not run, 1: run once directly, 2: captured
+    dirac_solver_stats delta{};
+  };
+  std::vector<Captured> cap(kmax);
+  const bool graphs = S.graphs;
+  auto run_step = [&](int k) -> int {
+    Captured& g = cap[k];
+    if (!graphs || g.state == 0) {
+      g.state = 1;
+      return step(k);
+    }
+    if (g.state == 2) {
+      if (cudaGraphLaunch(g.exec, S.st) != cudaSuccess) return set_err(S.c, DIRAC_ERR_CUDA, "GCR graph launch");
+      S.stats->dslash_calls += g.delta.dslash_calls;
+      S.stats->precond_calls += g.delta.precond_calls;
+      S.stats->flops += g.delta.flops;
+      return DIRAC_OK;
+    }
+    const dirac_solver_stats before = *S.stats;
+    if (cudaStreamBeginCapture(S.st, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+      return set_err(S.c, DIRAC_ERR_CUDA, "GCR graph capture");
+    const int rc = step(k);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(S.st, &graph);
+    if (rc || e != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      cudaGetLastError();
+      return rc ? rc : set_err(S.c, DIRAC_ERR_CUDA, "GCR graph capture");
+    }
+    const cudaError_t ei = cudaGraphInstantiate(&g.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ei != cudaSuccess) return set_err(S.c, DIRAC_ERR_CUDA, "GCR graph instantiate");
+    g.delta.dslash_calls = S.stats->dslash_calls - before.dslash_calls;
+    g.delta.precond_calls = S.stats->precond_calls - before.precond_calls;
+    g.delta.flops = S.stats->flops - before.flops;
+    g.state = 2;
+    if (cudaGraphLaunch(g.exec, S.st) != cudaSuccess) return set_err(S.c, DIRAC_ERR_CUDA, "GCR graph launch");
+    return DIRAC_OK;
+  };
+  struct ExecGuard {
+    std::vector<Captured>& v;
+    ~ExecGuard() {
+      for (auto& g : v)
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+    }
+  } guard{cap};
+  int k = 0;
+  while (r0n2 > target && S.stats->iters < P.max_iter) {
+    TRY(run_step(k));
     TRY(S.mark(k));
     ++k;
     S.stats->iters++;
@@ -836,8 +893,23 @@ extern "C" int solve(dirac_ctx* c, void* x, const void* b, const dirac_solver_pa
   dirac_solver_stats local{};
   dirac_solver_stats* st = stats ? stats : &local;
   *st = dirac_solver_stats{};
-  cudaStream_t s = (cudaStream_t)stream;
+  // The solve runs on the context's own non-blocking stream, ordered after the caller's
+  // stream: GCR captures its steps as CUDA graphs, which the legacy default stream
+  // cannot do. The call returns after the solve finished (synchronously).
+  cudaStream_t caller = (cudaStream_t)stream;
+  if (!c->solve_stream && cudaStreamCreateWithFlags(&c->solve_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    c->solve_stream = nullptr;
+    return set_err(c, DIRAC_ERR_CUDA, "solver stream");
+  }
+  if (!c->solve_event && cudaEventCreateWithFlags(&c->solve_event, cudaEventDisableTiming) != cudaSuccess) {
+    c->solve_event = nullptr;
+    return set_err(c, DIRAC_ERR_CUDA, "solver event");
+  }
+  cudaEventRecord(c->solve_event, caller);
+  cudaStreamWaitEvent(c->solve_stream, c->solve_event, 0);
+  cudaStream_t s = c->solve_stream;
   Ctx S{c, s, parity, which, 0, st, 0};
+  S.graphs = true;
   S.S = c->dscal;
   S.mirror = c->dmirror;
   S.hmirror = c->hmirror;
