@@ -178,6 +178,62 @@ __device__ __forceinline__ void tc_path_site(const Geom& g, const char* gauge, i
   else LinkIO<P32, R>::load(gauge, g.Vh, mu, 1 - par, ycb, U);
 }
 
+// Where path p >= 1 reads: the neighbour's checkerboard index and parity, the link's
+// plane and index in it, U or U^dagger, and the boundary sign (selects only).
+template <int R>
+__device__ __forceinline__ void tc_path_geom(const Geom& g, const char* gauge, int p, const int x[4], int par, int cb,
+                                             int& ycb, const char*& lplane, int& lidx, bool& dag, float& sgn) {
+  const int mu = (p - 1) >> 1;
+  dag = ((p - 1) & 1) != 0;
+  const int L = mu == 0 ? g.L[0] : mu == 1 ? g.L[1] : mu == 2 ? g.L[2] : g.L[3];
+  const int xm = mu == 0 ? x[0] : mu == 1 ? x[1] : mu == 2 ? x[2] : x[3];
+  const bool wrap = dag ? xm == 0 : xm + 1 == L;
+  const int ym = dag ? (wrap ? L - 1 : xm - 1) : (wrap ? 0 : xm + 1);
+  sgn = (wrap && mu == 3 && g.apbc) ? -1.f : 1.f;
+  const int y[4] = {mu == 0 ? ym : x[0], mu == 1 ? ym : x[1], mu == 2 ? ym : x[2], mu == 3 ? ym : x[3]};
+  ycb = cb_index(g, y);
+  const int lpar = dag ? 1 - par : par;
+  lplane = gauge + (size_t)(mu * 2 + lpar) * link_plane_bytes(R, 4, g.Vh);
+  lidx = dag ? ycb : cb;
+}
+
+template <int B>
+__device__ __forceinline__ void cp_async(uint32_t dst, const void* src) {
+  if constexpr (B == 16) asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src));
+  else if constexpr (B == 8) asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(src));
+  else asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(src));
+}
+
+// Per-thread prefetch buffer of one path: the c_in neighbour spinors ([chunk][thread],
+// 16 B chunks) then the link ([chunk][thread]); two of them alternate between paths.
+template <int CIN, int R>
+struct TcPrefetch {
+  using LIO = LinkIO<P32, R>;
+  static constexpr int SP_BYTES = CIN * 6 * TC_M * 16;
+  static constexpr int BUF = SP_BYTES + LIO::kChunks * TC_M * LIO::kChunkBytes;
+  static constexpr int BYTES = 2 * BUF;
+};
+
+template <int CIN, int R>
+__device__ __forceinline__ void tc_prefetch(uint8_t* buf, const char* const* in, size_t hb, int Vh, int ycb, int ypar,
+                                            const char* lplane, int lidx, bool link, int tid) {
+  using PF = TcPrefetch<CIN, R>;
+  const uint32_t b = smem_u32(buf);
+#pragma unroll
+  for (int ci = 0; ci < CIN; ++ci) {
+    const char* src = in[ci] + (size_t)ypar * hb;
+#pragma unroll
+    for (int k = 0; k < 6; ++k)
+      cp_async<16>(b + ((ci * 6 + k) * TC_M + tid) * 16, src + ((size_t)k * Vh + ycb) * 16);
+  }
+  if (link) {
+#pragma unroll
+    for (int k = 0; k < PF::LIO::kChunks; ++k)
+      cp_async<PF::LIO::kChunkBytes>(b + PF::SP_BYTES + (k * TC_M + tid) * PF::LIO::kChunkBytes,
+                                     lplane + ((size_t)k * Vh + lidx) * PF::LIO::kChunkBytes);
+  }
+}
+
 // Warp-specialised pipeline: warps 0-3 produce (transports, X_p rows), warp 4 issues the
 // MMAs. A ring of STAGES X_p buffers: full[s] completes when the 4 producer warps wrote
 // stage s, empty[s] when the MMAs that read it finished (tcgen05.commit). The tile's
@@ -204,8 +260,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) ptc_tc_layer_kernel(const TcArg
   __shared__ __align__(8) uint64_t full[TC_STAGES], empty[TC_STAGES], accf[2], acce[2], wbar, dbar;
   __shared__ uint32_t tmem_base_s;
   __shared__ volatile int abort_s;
+  using PF = TcPrefetch<CIN, R>;
   uint8_t* Bs = smem;
   uint8_t* As = smem + NPATH_TC * S::B_BYTES;
+  uint8_t* Ps = As + TC_STAGES * PP::STAGE_BYTES;  // two per-path prefetch buffers
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const Geom& g = a.g;
   const int Vh = g.Vh;
@@ -252,28 +310,45 @@ __global__ void __launch_bounds__(TC_THREADS, 1) ptc_tc_layer_kernel(const TcArg
       const int par = active && idx >= Vh ? 1 : 0, cb = active ? idx - par * Vh : 0;
       int x[4] = {0, 0, 0, 0};
       if (active) cb_coords(g, cb, par, x);
+      // path 0 (the site itself) goes to prefetch buffer 0; path p + 1 is requested
+      // while path p is computed
+      if (active) tc_prefetch<CIN, R>(Ps, a.in, hb, Vh, cb, par, nullptr, 0, false, tid);
+      asm volatile("cp.async.commit_group;");
+      bool dag_c = false, dag_n = false;
+      float sgn_c = 1.f, sgn_n = 1.f;
 #pragma unroll 1
       for (int p = 0; p < NPATH_TC; ++p, ++it) {
+        if (p + 1 < NPATH_TC) {
+          if (active) {
+            int ycb;
+            const char* lplane;
+            int lidx;
+            tc_path_geom<R>(g, a.gauge, p + 1, x, par, cb, ycb, lplane, lidx, dag_n, sgn_n);
+            tc_prefetch<CIN, R>(Ps + ((p + 1) & 1) * PF::BUF, a.in, hb, Vh, ycb, 1 - par, lplane, lidx, true, tid);
+          }
+          asm volatile("cp.async.commit_group;");
+          asm volatile("cp.async.wait_group 1;");
+        } else {
+          asm volatile("cp.async.wait_group 0;");
+        }
         const uint32_t st = it % TC_STAGES, ph = (it / TC_STAGES) & 1u;
         const bool late = !mbar_wait(&empty[st], ph ^ 1u);
         if (__any_sync(0xffffffffu, late || abort_s != 0)) {
           abort_s = 1;
+          asm volatile("cp.async.wait_group 0;");
           break;
         }
         C<float> t[CIN][12];
         if (active) {
-          int ycb = cb, ypar = par;
+          const uint8_t* buf = Ps + (p & 1) * PF::BUF;
           Link<float> U;
-          bool dag = false;
-          float sgn = 1.f;
-          if (p > 0) {
-            tc_path_site<R>(g, a.gauge, p, x, par, cb, ycb, U, dag, sgn);
-            ypar = 1 - par;
-          }
+          if (p > 0) LinkIO<P32, R>::template load_plane<false>(reinterpret_cast<const char*>(buf) + PF::SP_BYTES,
+                                                                TC_M, tid, U);
 #pragma unroll
           for (int ci = 0; ci < CIN; ++ci) {
             float v[24];
-            SpinorIO<P32, 24>::load(a.in[ci] + ypar * hb, Vh, ycb, v);
+            SpinorIO<P32, 24>::template load<false>(reinterpret_cast<const char*>(buf) + ci * 6 * TC_M * 16, TC_M,
+                                                    tid, v);
 #pragma unroll
             for (int s2 = 0; s2 < 4; ++s2) {
               C<float> f[3];
@@ -282,10 +357,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) ptc_tc_layer_kernel(const TcArg
               f[2] = C<float>{v[6 * s2 + 4], v[6 * s2 + 5]};
               if (p > 0) {
                 C<float> w3[3];
-                if (dag) su3_mv_dag(U, f, w3);
+                if (dag_c) su3_mv_dag(U, f, w3);
                 else su3_mv(U, f, w3);
 #pragma unroll
-                for (int c = 0; c < 3; ++c) t[ci][3 * s2 + c] = sgn * w3[c];
+                for (int c = 0; c < 3; ++c) t[ci][3 * s2 + c] = sgn_c * w3[c];
               } else {
 #pragma unroll
                 for (int c = 0; c < 3; ++c) t[ci][3 * s2 + c] = f[c];
@@ -298,6 +373,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) ptc_tc_layer_kernel(const TcArg
 #pragma unroll
             for (int k = 0; k < 12; ++k) t[ci][k] = C<float>{0.f, 0.f};
         }
+        dag_c = dag_n;
+        sgn_c = sgn_n;
         // this thread's rows of X_p (three colours): K = [Re (c', t) | Im (c', t)]
         uint8_t* stage = As + (size_t)st * PP::STAGE_BYTES;
 #pragma unroll
@@ -402,12 +479,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) ptc_tc_layer_kernel(const TcArg
 template <int CIN, int COUT, int R>
 int launch_tc(const TcArg& a, cudaStream_t st) {
   using PP = TcPipe<CIN, COUT>;
+  constexpr int SMEM = PP::SMEM + TcPrefetch<CIN, R>::BYTES;
   // once per instantiation: the shared-memory opt-in and the persistent grid (resident
   // CTAs per SM, capped so that every CTA gets its tensor memory)
   static int resident = 0;
   if (!resident) {
     if (cudaFuncSetAttribute(ptc_tc_layer_kernel<CIN, COUT, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             PP::SMEM) != cudaSuccess)
+                             SMEM) != cudaSuccess)
       return DIRAC_ERR_CUDA;
     int dev = 0, sms = 0, smem_sm = 0;
     cudaFuncAttributes fa{};
@@ -419,13 +497,13 @@ int launch_tc(const TcArg& a, cudaStream_t st) {
     // per CTA) and registers (allocated per warp in units of 256)
     const int regs_warp = ((fa.numRegs * 32 + 255) / 256) * 256;
     int per_sm = 512 / PP::TMEM;
-    per_sm = std::min(per_sm, smem_sm / (int)(PP::SMEM + fa.sharedSizeBytes + 1024));
+    per_sm = std::min(per_sm, smem_sm / (int)(SMEM + fa.sharedSizeBytes + 1024));
     per_sm = std::min(per_sm, 65536 / (regs_warp * (TC_THREADS / 32)));
     resident = sms * std::max(per_sm, 1);
   }
   int grid = resident;
   if (grid > a.ntiles) grid = a.ntiles;
-  ptc_tc_layer_kernel<CIN, COUT, R><<<grid, TC_THREADS, PP::SMEM, st>>>(a);
+  ptc_tc_layer_kernel<CIN, COUT, R><<<grid, TC_THREADS, SMEM, st>>>(a);
   return DIRAC_OK;
 }
 
