@@ -8,8 +8,8 @@
 //   X_p[m] = [Re (T_p in)(x_m)[c'][t][a] | Im ...]                       K = 2 KH
 //   B_p    = [[Re W, Im W], [-Im W, Re W]] over (c', t) x (c, s)          N = 2 NH
 // with KH = max(8, 4 c_in), NH = max(8, 4 c_out) (zero padding). One CTA of 128 threads
-// owns a tile: thread m computes the 8 parallel transports of its site (FP32 CUDA cores),
-// writes its rows of X_p (three colours) into shared memory in the canonical K-major
+// owns a tile: one thread per site and input channel computes the 8 parallel transports
+// of that spinor (FP32 CUDA cores), writes its columns of X_p (three colours) into shared memory in the canonical K-major
 // layout without swizzle (8x8 core matrices of 128 B; LBO 128 B along K, SBO 16 KC B
 // along the rows); a fifth warp issues tcgen05.mma for the three colours (accumulators
 // in 3 x N TMEM columns) as soon as a stage is full. Producers and the MMA warp meet
@@ -104,6 +104,16 @@ __device__ __forceinline__ void tmem_ld<16>(uint32_t taddr, float* v) {
       : "r"(taddr));
 #pragma unroll
   for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+template <>
+__device__ __forceinline__ void tmem_ld<4>(uint32_t taddr, float* v) {
+  uint32_t r[4];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(taddr));
+#pragma unroll
+  for (int j = 0; j < 4; ++j) v[j] = __uint_as_float(r[j]);
 }
 
 template <int CIN, int COUT>
@@ -204,8 +214,9 @@ __device__ __forceinline__ void cp_async(uint32_t dst, const void* src) {
   else asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(src));
 }
 
-// Per-thread prefetch buffer of one path: the c_in neighbour spinors ([chunk][thread],
-// 16 B chunks) then the link ([chunk][thread]); two of them alternate between paths.
+// Per-path prefetch buffer: every producer thread's neighbour spinor ([chunk][thread],
+// 16 B chunks), then the link of each site ([chunk][site], fetched by the site's first
+// thread); two of them alternate between paths.
 template <int CIN, int R>
 struct TcPrefetch {
   using LIO = LinkIO<P32, R>;
@@ -216,31 +227,40 @@ struct TcPrefetch {
 
 template <int CIN, int R>
 __device__ __forceinline__ void tc_prefetch(uint8_t* buf, const char* const* in, size_t hb, int Vh, int ycb, int ypar,
-                                            const char* lplane, int lidx, bool link, int tid) {
+                                            const char* lplane, int lidx, bool link, int q, int m) {
   using PF = TcPrefetch<CIN, R>;
+  constexpr int TPS = CIN == 4 ? 4 : 1, CPT = CIN / TPS, NT = TC_M * TPS;
   const uint32_t b = smem_u32(buf);
 #pragma unroll
-  for (int ci = 0; ci < CIN; ++ci) {
-    const char* src = in[ci] + (size_t)ypar * hb;
+  for (int cc = 0; cc < CPT; ++cc) {
+    const char* src = in[cc] + (size_t)ypar * hb;
 #pragma unroll
     for (int k = 0; k < 6; ++k)
-      cp_async<16>(b + ((ci * 6 + k) * TC_M + tid) * 16, src + ((size_t)k * Vh + ycb) * 16);
+      cp_async<16>(b + ((cc * 6 + k) * NT + q) * 16, src + ((size_t)k * Vh + ycb) * 16);
   }
   if (link) {
 #pragma unroll
     for (int k = 0; k < PF::LIO::kChunks; ++k)
-      cp_async<PF::LIO::kChunkBytes>(b + PF::SP_BYTES + (k * TC_M + tid) * PF::LIO::kChunkBytes,
+      cp_async<PF::LIO::kChunkBytes>(b + PF::SP_BYTES + (k * TC_M + m) * PF::LIO::kChunkBytes,
                                      lplane + ((size_t)k * Vh + lidx) * PF::LIO::kChunkBytes);
   }
 }
 
-// Warp-specialised pipeline: warps 0-3 produce (transports, X_p rows), warp 4 issues the
-// MMAs. A ring of STAGES X_p buffers: full[s] completes when the 4 producer warps wrote
-// stage s, empty[s] when the MMAs that read it finished (tcgen05.commit). The tile's
-// accumulators are double buffered in tensor memory: accf[b] completes when the MMAs of
-// a tile finished, acce[b] when the 4 producer warps read the results out.
-constexpr int TC_PROD = 4;
-constexpr int TC_THREADS = 32 * (TC_PROD + 1);
+// Warp-specialised pipeline: producer warps (TPS threads per site, each transporting CPT
+// input channels and writing their X_p columns), then one warp that issues the MMAs.
+// A ring of STAGES X_p buffers: full[s] completes when every producer warp wrote stage s,
+// empty[s] when the MMAs that read it finished (tcgen05.commit). The tile's accumulators
+// are double buffered in tensor memory: accf[b] completes when the MMAs of a tile
+// finished, acce[b] when every producer warp read its results out.
+template <int CIN>
+struct TcWarps {
+  // threads per site: one per input channel for c_in = 4 (measured faster); otherwise one
+  // thread does all channels of its site (the link and geometry work is per thread)
+  static constexpr int TPS = CIN == 4 ? 4 : 1;
+  static constexpr int CPT = CIN / TPS;  // channels per thread
+  static constexpr int PROD = 4 * TPS;
+  static constexpr int THREADS = 32 * (PROD + 1);
+};
 constexpr int TC_STAGES = 3;
 
 template <int CIN, int COUT>
@@ -253,14 +273,15 @@ struct TcPipe {
 };
 
 template <int CIN, int COUT, int R>
-__global__ void __launch_bounds__(TC_THREADS, 1) ptc_tc_layer_kernel(const TcArg a) {
+__global__ void __launch_bounds__(TcWarps<CIN>::THREADS, 1) ptc_tc_layer_kernel(const TcArg a) {
   using S = TcShape<CIN, COUT>;
   using PP = TcPipe<CIN, COUT>;
+  using PF = TcPrefetch<CIN, R>;
+  constexpr int PROD = TcWarps<CIN>::PROD, THREADS = TcWarps<CIN>::THREADS;
   extern __shared__ __align__(1024) uint8_t smem[];
   __shared__ __align__(8) uint64_t full[TC_STAGES], empty[TC_STAGES], accf[2], acce[2], wbar, dbar;
   __shared__ uint32_t tmem_base_s;
   __shared__ volatile int abort_s;
-  using PF = TcPrefetch<CIN, R>;
   uint8_t* Bs = smem;
   uint8_t* As = smem + NPATH_TC * S::B_BYTES;
   uint8_t* Ps = As + TC_STAGES * PP::STAGE_BYTES;  // two per-path prefetch buffers
@@ -277,12 +298,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) ptc_tc_layer_kernel(const TcArg
   if (tid == 0) {
     abort_s = 0;
     for (int i = 0; i < TC_STAGES; ++i) {
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&full[i])), "r"(TC_PROD));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&full[i])), "r"(PROD));
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&empty[i])), "r"(1));
     }
     for (int i = 0; i < 2; ++i) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&accf[i])), "r"(1));
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&acce[i])), "r"(TC_PROD));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&acce[i])), "r"(PROD));
     }
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&wbar)), "r"(1));
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&dbar)), "r"(1));
@@ -290,7 +311,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) ptc_tc_layer_kernel(const TcArg
   }
   // zero the X buffers once: padding columns (c_in = 1) are never written again and
   // must be finite (they meet zero rows of B)
-  for (int i = tid; i < TC_STAGES * PP::STAGE_BYTES / 16; i += TC_THREADS)
+  for (int i = tid; i < TC_STAGES * PP::STAGE_BYTES / 16; i += THREADS)
     reinterpret_cast<uint4*>(As)[i] = make_uint4(0u, 0u, 0u, 0u);
   asm volatile("fence.proxy.async.shared::cta;");
   asm volatile("tcgen05.fence::before_thread_sync;");
@@ -298,21 +319,31 @@ __global__ void __launch_bounds__(TC_THREADS, 1) ptc_tc_layer_kernel(const TcArg
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = tmem_base_s;
 
-  if (warp < TC_PROD) {
+  if (warp < PROD) {
     // ---------------------------------------------------------------- producers
+    constexpr int TPS = TcWarps<CIN>::TPS, CPT = TcWarps<CIN>::CPT;
+    const int q = tid, m = q / TPS, cg = q % TPS;  // site row of the tile, channel group
+    const char* inp[CPT];  // this thread's input channels cg * CPT + cc
+#pragma unroll
+    for (int cc = 0; cc < CPT; ++cc) {
+      inp[cc] = a.in[cc];
+#pragma unroll
+      for (int c = 1; c < TPS; ++c)
+        if (cg == c) inp[cc] = a.in[c * CPT + cc];
+    }
     uint32_t it = 0, tcount = 0;
     // abort decisions are warp-uniform (votes): the warp-wide tcgen05.ld and __syncwarp
     // below need every lane
     for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x, ++tcount) {
       if (__any_sync(0xffffffffu, abort_s != 0)) break;
-      const int idx = tile * TC_M + tid;
+      const int idx = tile * TC_M + m;
       const bool active = idx < 2 * Vh;
       const int par = active && idx >= Vh ? 1 : 0, cb = active ? idx - par * Vh : 0;
       int x[4] = {0, 0, 0, 0};
       if (active) cb_coords(g, cb, par, x);
       // path 0 (the site itself) goes to prefetch buffer 0; path p + 1 is requested
       // while path p is computed
-      if (active) tc_prefetch<CIN, R>(Ps, a.in, hb, Vh, cb, par, nullptr, 0, false, tid);
+      if (active) tc_prefetch<CIN, R>(Ps, inp, hb, Vh, cb, par, nullptr, 0, false, q, m);
       asm volatile("cp.async.commit_group;");
       bool dag_c = false, dag_n = false;
       float sgn_c = 1.f, sgn_n = 1.f;
@@ -324,13 +355,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1) ptc_tc_layer_kernel(const TcArg
             const char* lplane;
             int lidx;
             tc_path_geom<R>(g, a.gauge, p + 1, x, par, cb, ycb, lplane, lidx, dag_n, sgn_n);
-            tc_prefetch<CIN, R>(Ps + ((p + 1) & 1) * PF::BUF, a.in, hb, Vh, ycb, 1 - par, lplane, lidx, true, tid);
+            tc_prefetch<CIN, R>(Ps + ((p + 1) & 1) * PF::BUF, inp, hb, Vh, ycb, 1 - par, lplane, lidx, cg == 0, q, m);
           }
           asm volatile("cp.async.commit_group;");
           asm volatile("cp.async.wait_group 1;");
         } else {
           asm volatile("cp.async.wait_group 0;");
         }
+        __syncwarp();  // the site's link, fetched by its first thread, is visible to the others
         const uint32_t st = it % TC_STAGES, ph = (it / TC_STAGES) & 1u;
         const bool late = !mbar_wait(&empty[st], ph ^ 1u);
         if (__any_sync(0xffffffffu, late || abort_s != 0)) {
@@ -338,17 +370,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1) ptc_tc_layer_kernel(const TcArg
           asm volatile("cp.async.wait_group 0;");
           break;
         }
-        C<float> t[CIN][12];
+        C<float> t[CPT][12];
         if (active) {
-          const uint8_t* buf = Ps + (p & 1) * PF::BUF;
+          const char* buf = reinterpret_cast<const char*>(Ps + (p & 1) * PF::BUF);
           Link<float> U;
-          if (p > 0) LinkIO<P32, R>::template load_plane<false>(reinterpret_cast<const char*>(buf) + PF::SP_BYTES,
-                                                                TC_M, tid, U);
+          if (p > 0) LinkIO<P32, R>::template load_plane<false>(buf + PF::SP_BYTES, TC_M, m, U);
 #pragma unroll
-          for (int ci = 0; ci < CIN; ++ci) {
+          for (int cc = 0; cc < CPT; ++cc) {
             float v[24];
-            SpinorIO<P32, 24>::template load<false>(reinterpret_cast<const char*>(buf) + ci * 6 * TC_M * 16, TC_M,
-                                                    tid, v);
+            SpinorIO<P32, 24>::template load<false>(buf + cc * 6 * TC_M * TPS * 16, TC_M * TPS, q, v);
 #pragma unroll
             for (int s2 = 0; s2 < 4; ++s2) {
               C<float> f[3];
@@ -360,45 +390,49 @@ __global__ void __launch_bounds__(TC_THREADS, 1) ptc_tc_layer_kernel(const TcArg
                 if (dag_c) su3_mv_dag(U, f, w3);
                 else su3_mv(U, f, w3);
 #pragma unroll
-                for (int c = 0; c < 3; ++c) t[ci][3 * s2 + c] = sgn_c * w3[c];
+                for (int c = 0; c < 3; ++c) t[cc][3 * s2 + c] = sgn_c * w3[c];
               } else {
 #pragma unroll
-                for (int c = 0; c < 3; ++c) t[ci][3 * s2 + c] = f[c];
+                for (int c = 0; c < 3; ++c) t[cc][3 * s2 + c] = f[c];
               }
             }
           }
         } else {
 #pragma unroll
-          for (int ci = 0; ci < CIN; ++ci)
+          for (int cc = 0; cc < CPT; ++cc)
 #pragma unroll
-            for (int k = 0; k < 12; ++k) t[ci][k] = C<float>{0.f, 0.f};
+            for (int k = 0; k < 12; ++k) t[cc][k] = C<float>{0.f, 0.f};
         }
         dag_c = dag_n;
         sgn_c = sgn_n;
-        // this thread's rows of X_p (three colours): K = [Re (c', t) | Im (c', t)]
+        // this thread's columns of row m of X_p (three colours): the 4 spins of each of
+        // its channels ci, real part at K = 4 ci, imaginary part at KH + 4 ci
         uint8_t* stage = As + (size_t)st * PP::STAGE_BYTES;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
           uint8_t* A = stage + (size_t)c * S::A_BYTES;
 #pragma unroll
-          for (int h = 0; h < 2; ++h)        // real, imaginary half of K
+          for (int cc = 0; cc < CPT; ++cc) {
+            const int ci = cg * CPT + cc;
 #pragma unroll
-            for (int ci = 0; ci < CIN; ++ci) {  // 4 spins of input channel ci: 8 bytes
-              float q[4];
+            for (int h = 0; h < 2; ++h) {
+              float qv[4];
 #pragma unroll
-              for (int t4 = 0; t4 < 4; ++t4) q[t4] = h ? t[ci][3 * t4 + c].i : t[ci][3 * t4 + c].r;
-              const __nv_bfloat162 lo = __floats2bfloat162_rn(q[0], q[1]);
-              const __nv_bfloat162 hi = __floats2bfloat162_rn(q[2], q[3]);
-              *reinterpret_cast<uint2*>(A + canon_off(tid, h * S::KH + 4 * ci, S::KC)) =
+              for (int t4 = 0; t4 < 4; ++t4) qv[t4] = h ? t[cc][3 * t4 + c].i : t[cc][3 * t4 + c].r;
+              const __nv_bfloat162 lo = __floats2bfloat162_rn(qv[0], qv[1]);
+              const __nv_bfloat162 hi = __floats2bfloat162_rn(qv[2], qv[3]);
+              *reinterpret_cast<uint2*>(A + canon_off(m, h * S::KH + 4 * ci, S::KC)) =
                   make_uint2(*reinterpret_cast<const uint32_t*>(&lo), *reinterpret_cast<const uint32_t*>(&hi));
             }
+          }
         }
         asm volatile("fence.proxy.async.shared::cta;");
         __syncwarp();
         if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&full[st])));
       }
       if (__any_sync(0xffffffffu, abort_s != 0)) break;
-      // the tile's results: wait for its MMAs, read this warp's 32 lanes (sites)
+      // the tile's results: warp w reads lane quarter w % 4 (sites 32 (w % 4) + lane) and
+      // stores the output channels co = w / 4 (mod TPS)
       const uint32_t b = tcount & 1u, pb = (tcount >> 1) & 1u;
       const bool late = !mbar_wait(&accf[b], pb);
       if (__any_sync(0xffffffffu, late || abort_s != 0)) {
@@ -406,32 +440,68 @@ __global__ void __launch_bounds__(TC_THREADS, 1) ptc_tc_layer_kernel(const TcArg
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;");
-      float d[3][S::N];
-      const uint32_t base = tmem + ((uint32_t)(warp * 32) << 16) + b * PP::ACC_COLS;
+      const int quarter = warp & 3, grp = warp >> 2;
+      const uint32_t base = tmem + ((uint32_t)(quarter * 32) << 16) + b * PP::ACC_COLS;
+      const int oidx = tile * TC_M + quarter * 32 + lane;
+      const bool oact = oidx < 2 * Vh;
+      const int opar = oact && oidx >= Vh ? 1 : 0, ocb = oact ? oidx - opar * Vh : 0;
+      if constexpr (S::N == 16) {
+        // all 16 columns of each colour at once (48 registers)
+        float d[3][16];
 #pragma unroll
-      for (int c = 0; c < 3; ++c) tmem_ld<S::N>(base + c * S::N, d[c]);
-      asm volatile("tcgen05.wait::ld.sync.aligned;");
-      asm volatile("tcgen05.fence::before_thread_sync;");
-      __syncwarp();
-      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acce[b])));
-      if (active) {
+        for (int c = 0; c < 3; ++c) tmem_ld<16>(base + c * S::N, d[c]);
+        asm volatile("tcgen05.wait::ld.sync.aligned;");
+        // the accumulator is free as soon as it is in registers
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        __syncwarp();
+        if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acce[b])));
+        if (oact) {
+#pragma unroll
+          for (int co = 0; co < COUT; ++co) {
+            if (co % TPS != grp) continue;
+            float o[24];
+#pragma unroll
+            for (int s2 = 0; s2 < 4; ++s2)
+#pragma unroll
+              for (int c = 0; c < 3; ++c) {
+                o[6 * s2 + 2 * c] = d[c][co * 4 + s2];
+                o[6 * s2 + 2 * c + 1] = d[c][S::NH + co * 4 + s2];
+              }
+            SpinorIO<P32, 24>::store(a.out[co] + opar * hb, Vh, ocb, o);
+          }
+        }
+      } else {
+        // per output channel: 4 real and 4 imaginary columns of each colour
 #pragma unroll
         for (int co = 0; co < COUT; ++co) {
-          float o[24];
+          if (co % TPS != grp) continue;  // warp-uniform
+          float re[3][4], im[3][4];
 #pragma unroll
-          for (int s2 = 0; s2 < 4; ++s2)
+          for (int c = 0; c < 3; ++c) {
+            tmem_ld<4>(base + c * S::N + co * 4, re[c]);
+            tmem_ld<4>(base + c * S::N + S::NH + co * 4, im[c]);
+          }
+          asm volatile("tcgen05.wait::ld.sync.aligned;");
+          if (oact) {
+            float o[24];
 #pragma unroll
-            for (int c = 0; c < 3; ++c) {
-              o[6 * s2 + 2 * c] = d[c][co * 4 + s2];
-              o[6 * s2 + 2 * c + 1] = d[c][S::NH + co * 4 + s2];
-            }
-          SpinorIO<P32, 24>::store(a.out[co] + par * hb, Vh, cb, o);
+            for (int s2 = 0; s2 < 4; ++s2)
+#pragma unroll
+              for (int c = 0; c < 3; ++c) {
+                o[6 * s2 + 2 * c] = re[c][s2];
+                o[6 * s2 + 2 * c + 1] = im[c][s2];
+              }
+            SpinorIO<P32, 24>::store(a.out[co] + opar * hb, Vh, ocb, o);
+          }
         }
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        __syncwarp();
+        if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acce[b])));
       }
     }
   } else if (lane == 0) {
     // ---------------------------------------------------------------- MMA issuer
-    if (tid == 32 * TC_PROD) {
+    {
       const uint32_t bytes = NPATH_TC * S::B_BYTES;
       asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&wbar)), "r"(bytes));
       asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
@@ -498,12 +568,12 @@ int launch_tc(const TcArg& a, cudaStream_t st) {
     const int regs_warp = ((fa.numRegs * 32 + 255) / 256) * 256;
     int per_sm = 512 / PP::TMEM;
     per_sm = std::min(per_sm, smem_sm / (int)(SMEM + fa.sharedSizeBytes + 1024));
-    per_sm = std::min(per_sm, 65536 / (regs_warp * (TC_THREADS / 32)));
+    per_sm = std::min(per_sm, 65536 / (regs_warp * (TcWarps<CIN>::THREADS / 32)));
     resident = sms * std::max(per_sm, 1);
   }
   int grid = resident;
   if (grid > a.ntiles) grid = a.ntiles;
-  ptc_tc_layer_kernel<CIN, COUT, R><<<grid, TC_THREADS, SMEM, st>>>(a);
+  ptc_tc_layer_kernel<CIN, COUT, R><<<grid, TcWarps<CIN>::THREADS, SMEM, st>>>(a);
   return DIRAC_OK;
 }
 
