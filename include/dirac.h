@@ -100,7 +100,11 @@ int dirac_load_gauge(dirac_ctx* ctx, const double* links, int which, int on_devi
 
 /* Convert a spinor between the natural FP64 layout (host or device) and the device
  * layout of precision `prec`. For a parity half-field only the sites of that parity
- * are read (import) or written (export); the natural array always spans the lattice. */
+ * are read (import) or written (export); the natural array always spans the lattice.
+ * With FP64 or FP32 storage, a host array in page-locked memory (or any host memory
+ * where the GPU uses the host's page tables) is accessed in place by the conversion
+ * kernel; other host memory, and FP16 storage, go through a device staging copy. Calls with a host array return after it has been
+ * read / written. */
 int dirac_import_spinor(dirac_ctx* ctx, void* dst, dirac_prec prec, dirac_parity parity,
                         const double* src_natural, int src_on_device, void* stream);
 int dirac_export_spinor(dirac_ctx* ctx, double* dst_natural, int dst_on_device,

@@ -334,7 +334,24 @@ static int spinor_xfer(dirac_ctx* c, bool import, void* dev, dirac_prec prec, di
   double* d = nat_ptr;
   char* staging = nullptr;
   int rc;
-  if (!nat_on_device) {
+  // Page-locked host memory (and, on systems where the GPU shares the host's page
+  // tables, any host memory) is read and written in place over the host link by
+  // coalesced conversion kernels (FP64 / FP32 storage): no staging copy, one pass.
+  bool direct = false;
+  if (!nat_on_device && prec != P16) {
+    cudaPointerAttributes pa{};
+    if (cudaPointerGetAttributes(&pa, nat_ptr) == cudaSuccess && pa.type == cudaMemoryTypeHost && pa.devicePointer) {
+      d = (double*)pa.devicePointer;
+      direct = true;
+    } else {
+      cudaGetLastError();
+      int dev = 0, pageable = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&pageable, cudaDevAttrPageableMemoryAccessUsesHostPageTables, dev);
+      direct = pageable != 0;
+    }
+  }
+  if (!nat_on_device && !direct) {
     if (c->staging_bytes < nat) {
       if (c->staging) cudaFree(c->staging);
       c->staging = nullptr;
@@ -348,9 +365,14 @@ static int spinor_xfer(dirac_ctx* c, bool import, void* dev, dirac_prec prec, di
     // sites come back unchanged
     if (import || parity != DIRAC_PARITY_FULL) cudaMemcpyAsync(d, nat_ptr, nat, cudaMemcpyHostToDevice, st);
   }
-  if (import) launch_import_spinor(prec, c->nr, (char*)dev, parity, d, c->g, st);
+  if (direct) launch_host_spinor(import, prec, c->nr, (char*)dev, parity, d, c->g, st);
+  else if (import) launch_import_spinor(prec, c->nr, (char*)dev, parity, d, c->g, st);
   else launch_export_spinor(prec, c->nr, d, parity, (const char*)dev, c->g, st);
   rc = cuda_check(c, import ? "import spinor" : "export spinor");
+  if (direct) {
+    cudaStreamSynchronize(st);  // the host buffer is read / written on return
+    if (!rc) rc = cuda_check(c, "spinor host access");
+  }
   if (staging) {
     if (!import && !rc) cudaMemcpyAsync(nat_ptr, d, nat, cudaMemcpyDeviceToHost, st);
     cudaStreamSynchronize(st);  // the host buffer is free for reuse on return

@@ -56,6 +56,10 @@ void launch_export_spinor(int prec, int nr, double* dst, int parity, const char*
                           cudaStream_t st);
 void launch_pack_links(int prec, int recon, char* dst, const double* src, const Geom& g,
                        cudaStream_t st);
+// natural FP64 array in host memory the GPU can access <-> device layout, coalesced over
+// the host link (FP64 / FP32 storage; returns false for FP16, which uses a staging copy)
+bool launch_host_spinor(bool import, int prec, int nr, char* dev, int parity, double* nat, const Geom& g,
+                        cudaStream_t st);
 // Ahat = 1 + 2 kappa A into dst[p]; Ahat^-1 into inv[p] when inv is not null
 void launch_build_clover(const double* links, const Geom& g, double kappa, double csw,
                          char* const dst[3], char* const inv[3], unsigned prec_mask, cudaStream_t st);
