@@ -175,6 +175,14 @@ __device__ __forceinline__ float site_norm_scale(const float* v, int n, float& i
 
 template <> struct SpinorIO<P16, 24> {
   __host__ __device__ static constexpr size_t half_bytes(int64_t Vh) { return (size_t)52 * Vh; }
+  // the 24 stored values without the per-site norm, which is returned
+  template <bool NC = true>
+  __device__ static float load_raw(const char* b, int Vh, int cb, float v[24]) {
+    const float n = ld_chunk<float, NC>(b + (size_t)48 * Vh + (size_t)cb * 4);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) unpack_half8(ld_chunk<int4, NC>(b + ((size_t)k * Vh + cb) * 16), v + 8 * k);
+    return n;
+  }
   template <bool NC = true>
   __device__ static void load(const char* b, int Vh, int cb, float v[24]) {
     float n = ld_chunk<float, NC>(b + (size_t)48 * Vh + (size_t)cb * 4);
@@ -200,6 +208,17 @@ template <> struct SpinorIO<P16, 24> {
 
 template <> struct SpinorIO<P16, 6> {
   __host__ __device__ static constexpr size_t half_bytes(int64_t Vh) { return (size_t)16 * Vh; }
+  // the 6 stored values without the per-site norm, which is returned
+  template <bool NC = true>
+  __device__ static float load_raw(const char* b, int Vh, int cb, float v[6]) {
+    const float n = ld_chunk<float, NC>(b + (size_t)12 * Vh + (size_t)cb * 4);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const float2 q = __half22float2(ld_chunk<__half2, NC>(b + ((size_t)k * Vh + cb) * 4));
+      v[2 * k] = q.x; v[2 * k + 1] = q.y;
+    }
+    return n;
+  }
   template <bool NC = true>
   __device__ static void load(const char* b, int Vh, int cb, float v[6]) {
     float n = ld_chunk<float, NC>(b + (size_t)12 * Vh + (size_t)cb * 4);

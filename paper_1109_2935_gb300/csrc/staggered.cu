@@ -34,6 +34,18 @@ __device__ __forceinline__ int stag_shift(int v, int n, int L, int& wraps) {
   return v;
 }
 
+// A neighbour spinor and the factor its link product is multiplied by: with FP16 storage
+// the per-site norm is left out of the 6 values and folded into that factor.
+template <int PREC, typename T>
+__device__ __forceinline__ T load_stag_spinor(const char* src, int Vh, int cb, T v[6]) {
+  if constexpr (PREC == P16) {
+    return SpinorIO<P16, 6>::load_raw(src, Vh, cb, v);
+  } else {
+    SpinorIO<PREC, 6>::load(src, Vh, cb, v);
+    return (T)1;
+  }
+}
+
 template <int PREC, int RL>
 __global__ void __launch_bounds__(128) staggered_kernel(const StagArg a) {
   using T = typename Real<PREC>::T;
@@ -60,13 +72,13 @@ __global__ void __launch_bounds__(128) staggered_kernel(const StagArg a) {
         y[mu] = stag_shift(x[mu], n, g.L[mu], w);
         T bc = (mu == 3 && g.apbc && (w & 1)) ? (T)-1 : (T)1;
         T v[6];
-        SpinorIO<PREC, 6>::load(a.in, Vh, cb_index(g, y), v);
+        const T nrm = load_stag_spinor<PREC, T>(a.in, Vh, cb_index(g, y), v);
         C<T> h[3] = {{v[0], v[1]}, {v[2], v[3]}, {v[4], v[5]}}, r[3];
         Link<T> U;
         if (hop == 0) LinkIO<PREC, 18>::load(links, Vh, mu, par, cb, U);
         else LinkIO<PREC, RL>::load(links, Vh, mu, par, cb, U);
         su3_mv(U, h, r);
-        const T f = eta * bc;
+        const T f = eta * bc * nrm;
 #pragma unroll
         for (int c = 0; c < 3; ++c) acc[c] = acc[c] + f * r[c];
       }
@@ -77,13 +89,13 @@ __global__ void __launch_bounds__(128) staggered_kernel(const StagArg a) {
         T bc = (mu == 3 && g.apbc && (w & 1)) ? (T)-1 : (T)1;
         int ycb = cb_index(g, y);
         T v[6];
-        SpinorIO<PREC, 6>::load(a.in, Vh, ycb, v);
+        const T nrm = load_stag_spinor<PREC, T>(a.in, Vh, ycb, v);
         C<T> h[3] = {{v[0], v[1]}, {v[2], v[3]}, {v[4], v[5]}}, r[3];
         Link<T> U;
         if (hop == 0) LinkIO<PREC, 18>::load(links, Vh, mu, 1 - par, ycb, U);
         else LinkIO<PREC, RL>::load(links, Vh, mu, 1 - par, ycb, U);
         su3_mv_dag(U, h, r);
-        const T f = -eta * bc;
+        const T f = -eta * bc * nrm;
 #pragma unroll
         for (int c = 0; c < 3; ++c) acc[c] = acc[c] + f * r[c];
       }

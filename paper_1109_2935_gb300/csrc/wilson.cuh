@@ -34,6 +34,19 @@ struct WilsonArg {
   double s = 1.0;
 };
 
+// A neighbour spinor for wilson_hop and the factor that multiplies its projection: with
+// FP16 storage the per-site norm is left out of the 24 values and folded into that
+// factor (one multiply per projected component instead of one per stored value).
+template <int PREC, typename T>
+__device__ __forceinline__ T load_hop_spinor(const char* src, int Vh, int cb, T psi[24], T bc) {
+  if constexpr (PREC == P16) {
+    return bc * SpinorIO<P16, 24>::load_raw(src, Vh, cb, psi);
+  } else {
+    SpinorIO<PREC, 24>::load(src, Vh, cb, psi);
+    return bc;
+  }
+}
+
 template <int MU, typename T>
 __device__ __forceinline__ void wilson_hop(C<T> acc[4][3], const T* psi, const Link<T>& U,
                                            bool link_dag, T s, T bc) {
@@ -192,7 +205,7 @@ __device__ __forceinline__ void wilson_site(const WilsonArg& a, int idx) {
         if (mu == 3 && g.apbc) bc = -1;
       }
       T psi[24];
-      SpinorIO<PREC, 24>::load(src, Vh, cb_index(g, y), psi);
+      bc = load_hop_spinor<PREC, T>(src, Vh, cb_index(g, y), psi, bc);
       Link<T> U;
       LinkIO<PREC, R>::load(a.gauge, Vh, mu, par, cb, U);
       if (mu == 0) wilson_hop<0>(acc, psi, U, false, sf, bc);
@@ -210,7 +223,7 @@ __device__ __forceinline__ void wilson_site(const WilsonArg& a, int idx) {
       }
       int ycb = cb_index(g, y);
       T psi[24];
-      SpinorIO<PREC, 24>::load(src, Vh, ycb, psi);
+      bc = load_hop_spinor<PREC, T>(src, Vh, ycb, psi, bc);
       Link<T> U;
       LinkIO<PREC, R>::load(a.gauge, Vh, mu, 1 - par, ycb, U);
       if (mu == 0) wilson_hop<0>(acc, psi, U, true, sb, bc);
