@@ -398,6 +398,61 @@ int solve_cg(Ctx& S, char* x, const char* b, const dirac_solver_params& P) {
 }
 
 // ------------------------------------------------------------------ BiCGstab (Sec. 3.1)
+// Replay of solver steps as CUDA graphs. A step whose launches depend only on a small
+// key (the Krylov index of GCR, the mirror slot of BiCGstab) runs directly the first time
+// (allocations and one-time attributes happen then), is captured the second time and
+// replayed afterwards; the statistics it adds on the host are recorded at capture and
+// added on replay.
+struct StepGraphs {
+  struct G {
+    cudaGraphExec_t exec = nullptr;
+    int state = 0;  // 0: not run, 1: run once directly, 2: captured
+    dirac_solver_stats delta{};
+  };
+  std::vector<G> g;
+  bool on;
+  StepGraphs(int n, bool enable) : g(n), on(enable) {}
+  ~StepGraphs() {
+    for (auto& x : g)
+      if (x.exec) cudaGraphExecDestroy(x.exec);
+  }
+  template <class F>
+  int run(Ctx& S, int key, F&& step) {
+    G& e = g[key];
+    if (!on || e.state == 0) {
+      e.state = 1;
+      return step();
+    }
+    if (e.state == 2) {
+      if (cudaGraphLaunch(e.exec, S.st) != cudaSuccess) return set_err(S.c, DIRAC_ERR_CUDA, "graph launch");
+      S.stats->dslash_calls += e.delta.dslash_calls;
+      S.stats->precond_calls += e.delta.precond_calls;
+      S.stats->flops += e.delta.flops;
+      return DIRAC_OK;
+    }
+    const dirac_solver_stats before = *S.stats;
+    if (cudaStreamBeginCapture(S.st, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+      return set_err(S.c, DIRAC_ERR_CUDA, "graph capture");
+    const int rc = step();
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(S.st, &graph);
+    if (rc || ec != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      cudaGetLastError();
+      return rc ? rc : set_err(S.c, DIRAC_ERR_CUDA, "graph capture");
+    }
+    const cudaError_t ei = cudaGraphInstantiate(&e.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ei != cudaSuccess) return set_err(S.c, DIRAC_ERR_CUDA, "graph instantiate");
+    e.delta.dslash_calls = S.stats->dslash_calls - before.dslash_calls;
+    e.delta.precond_calls = S.stats->precond_calls - before.precond_calls;
+    e.delta.flops = S.stats->flops - before.flops;
+    e.state = 2;
+    if (cudaGraphLaunch(e.exec, S.st) != cudaSuccess) return set_err(S.c, DIRAC_ERR_CUDA, "graph launch");
+    return DIRAC_OK;
+  }
+};
+
 int solve_bicgstab(Ctx& S, char* x, const char* b, const dirac_solver_params& P) {
   Blas* B = S.c->blas;
   const int sp = P.prec_sloppy, ap = accum_prec(sp);
@@ -425,7 +480,8 @@ int solve_bicgstab(Ctx& S, char* x, const char* b, const dirac_solver_params& P)
   double rmax = rr;
   int it = 0;
   bool converged = false;
-  while (S.stats->iters < P.max_iter) {
+  // one iteration; its launches depend only on the mirror slot it & 1
+  auto step = [&](int slot) -> int {
     KC((k_bicg1<<<1, 1, 0, S.st>>>(S.S)));
     // p = r + beta (p - omega v)
     BT(blas_pupdate(B, S.f(rs, sp), cptr(S.slot(S_BETA)), cptr(S.slot(S_NBW)), S.f(v, sp), S.f(p, sp), S.st));
@@ -441,7 +497,12 @@ int solve_bicgstab(Ctx& S, char* x, const char* b, const dirac_solver_params& P)
     BT(blas_bicg_xr(B, cptr(S.slot(S_ALPHA)), S.f(p, sp), cptr(S.slot(S_OMEGA)), S.f(rs, sp),
                     cptr(S.slot(S_NOMEGA)), S.f(t, sp), S.f(xs, ap), S.f(r0, sp), nullptr, S.st,
                     S.slot(S_RN)));
-    KC((k_bicg4<<<1, 1, 0, S.st>>>(S.S, S.mirror, it & 1, it)));
+    KC((k_bicg4<<<1, 1, 0, S.st>>>(S.S, S.mirror, slot, slot)));
+    return DIRAC_OK;
+  };
+  StepGraphs graphs(2, S.graphs);
+  while (S.stats->iters < P.max_iter) {
+    TRY(graphs.run(S, it & 1, [&] { return step(it & 1); }));
     TRY(S.mark(it));
     S.stats->iters++;
     if (it > 0) {
@@ -555,8 +616,7 @@ int solve_gcr(Ctx& S, char* x, const char* b, const dirac_solver_params& P, int 
   auto gb = [&](int i, int k) { return S.slot(S_GB + 4 * (i * KMAX + k) + 1); };
   // One GCR step at Krylov index k: p_k = K r_k, z_k = M p_k, orthogonalisation, the
   // residual update. Its launches depend only on k, so from the second restart cycle on
-  // each step replays a CUDA graph captured the cycle before (fewer host launches;
-  // statistics are added as the captured step counted them).
+  // each step replays a CUDA graph captured the cycle before.
   auto step = [&](int k) -> int {
     // p_k = K r_k
     if (kind != K_NONE) {
@@ -588,57 +648,10 @@ int solve_gcr(Ctx& S, char* x, const char* b, const dirac_solver_params& P, int 
     KC((k_mirror<<<1, 1, 0, S.st>>>(S.S, S_RH, S.mirror, k & 1, k)));
     return DIRAC_OK;
   };
-  struct Captured {
-    cudaGraphExec_t exec = nullptr;
-    int state = 0;  // 0: not run, 1: run once directly, 2: captured
-    dirac_solver_stats delta{};
-  };
-  std::vector<Captured> cap(kmax);
-  const bool graphs = S.graphs;
-  auto run_step = [&](int k) -> int {
-    Captured& g = cap[k];
-    if (!graphs || g.state == 0) {
-      g.state = 1;
-      return step(k);
-    }
-    if (g.state == 2) {
-      if (cudaGraphLaunch(g.exec, S.st) != cudaSuccess) return set_err(S.c, DIRAC_ERR_CUDA, "GCR graph launch");
-      S.stats->dslash_calls += g.delta.dslash_calls;
-      S.stats->precond_calls += g.delta.precond_calls;
-      S.stats->flops += g.delta.flops;
-      return DIRAC_OK;
-    }
-    const dirac_solver_stats before = *S.stats;
-    if (cudaStreamBeginCapture(S.st, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
-      return set_err(S.c, DIRAC_ERR_CUDA, "GCR graph capture");
-    const int rc = step(k);
-    cudaGraph_t graph = nullptr;
-    const cudaError_t e = cudaStreamEndCapture(S.st, &graph);
-    if (rc || e != cudaSuccess) {
-      if (graph) cudaGraphDestroy(graph);
-      cudaGetLastError();
-      return rc ? rc : set_err(S.c, DIRAC_ERR_CUDA, "GCR graph capture");
-    }
-    const cudaError_t ei = cudaGraphInstantiate(&g.exec, graph, 0);
-    cudaGraphDestroy(graph);
-    if (ei != cudaSuccess) return set_err(S.c, DIRAC_ERR_CUDA, "GCR graph instantiate");
-    g.delta.dslash_calls = S.stats->dslash_calls - before.dslash_calls;
-    g.delta.precond_calls = S.stats->precond_calls - before.precond_calls;
-    g.delta.flops = S.stats->flops - before.flops;
-    g.state = 2;
-    if (cudaGraphLaunch(g.exec, S.st) != cudaSuccess) return set_err(S.c, DIRAC_ERR_CUDA, "GCR graph launch");
-    return DIRAC_OK;
-  };
-  struct ExecGuard {
-    std::vector<Captured>& v;
-    ~ExecGuard() {
-      for (auto& g : v)
-        if (g.exec) cudaGraphExecDestroy(g.exec);
-    }
-  } guard{cap};
+  StepGraphs cap(kmax, S.graphs);
   int k = 0;
   while (r0n2 > target && S.stats->iters < P.max_iter) {
-    TRY(run_step(k));
+    TRY(cap.run(S, k, [&] { return step(k); }));
     TRY(S.mark(k));
     ++k;
     S.stats->iters++;
