@@ -77,6 +77,69 @@ def test_wilson_dslash_24x128_f32(dirac, wilson_full, parity):
     check(_at(got, s), ref, F32, 24, f"24^3x128 D_{parity}")
 
 
+def _sampled_residual(Un, csw, kappa, b, x, dims, n=512, seed=9):
+    """||b - M x|| / ||b|| over a random sample of sites (plus the corners), the oracle
+    evaluating M one site at a time: an estimate of the true residual that does not use
+    the library's own FP64 residual."""
+    s = _sample(dims, n, seed=seed)
+    mx = wilson.apply_M_sites(Un, csw, kappa, x, s, True, False)
+    bs = _at(b, s)
+    return np.linalg.norm(bs - mx) / np.linalg.norm(bs)
+
+
+@pytest.mark.parametrize("alg,sloppy,precond,kappa", [
+    ("BICGSTAB_EO", F16, F16, 0.124),
+    ("GCR_DD", F16, F16, 0.124),
+])
+def test_solves_24x128_reach_1e10(dirac, alg, sloppy, precond, kappa):
+    """Mixed-precision solves of the 24^3x128 workload as the benchmark runs them: the
+    library's FP64 true residual <= 1e-10, and the oracle's sampled residual agrees."""
+    dims = (24, 24, 24, 128)
+    U = synth.wilson_gauge(dims, 0.5, 3, 2001, device="cuda")
+    b = synth.wilson_spinor(dims, 2002, device="cuda")
+    lat = dirac.Lattice(dims, dirac.WILSON_CLOVER, kappa=kappa, csw=1.0, block=(4, 4, 4, 4), mr_steps=6,
+                        recon=(18, 12, 12))
+    lat.load_gauge(U)
+    fb = lat.to_device(b, F64)
+    fx = lat.new_field(F64)
+    st = lat.solve(fx, fb, getattr(dirac, alg), tol=1e-10, max_iter=4000, k_max=16, delta=0.1,
+                   prec_sloppy=sloppy, prec_precond=precond)
+    assert st["true_rel_resid"] <= 1e-10
+    x = lat.to_natural(fx, F64, device="cpu").numpy()
+    est = _sampled_residual(U.cpu().numpy(), 1.0, kappa, b.cpu().numpy(), x, dims)
+    assert est < 1e-9, est
+    lat.close()
+
+
+def test_learned_preconditioner_solve_24x128_kappa_0135(dirac):
+    """At kappa 0.1350 (the workload as configured), GCR with a PTC network trained on a
+    16^4 field at the same kappa and applied unchanged to 24^3x128 reaches 1e-10; the
+    oracle's sampled residual agrees."""
+    import bench
+    dims = (24, 24, 24, 128)
+    kappa = 0.135
+    plat, pnet, _, _, _ = bench.train_ptc(dirac, synth, torch.device("cuda"), kappa)
+    w = pnet.get_weights()
+    plat.close()
+    U = synth.wilson_gauge(dims, 0.5, 3, 2001, device="cuda")
+    b = synth.wilson_spinor(dims, 2002, device="cuda")
+    lat = dirac.Lattice(dims, dirac.WILSON_CLOVER, kappa=kappa, csw=1.0, block=(4, 4, 4, 4), mr_steps=6,
+                        recon=(18, 12, 12))
+    lat.load_gauge(U)
+    net = dirac.Ptc(lat, bench.PTC_CHANNELS)
+    net.set_weights(w)
+    net.attach(force=True)
+    fb = lat.to_device(b, F64)
+    fx = lat.new_field(F64)
+    st = lat.solve(fx, fb, dirac.GCR_PTC, tol=1e-10, max_iter=2000, k_max=16, delta=0.1,
+                   prec_sloppy=F32, prec_precond=F32)
+    assert st["true_rel_resid"] <= 1e-10 and st["precond"] == "ptc"
+    x = lat.to_natural(fx, F64, device="cpu").numpy()
+    est = _sampled_residual(U.cpu().numpy(), 1.0, kappa, b.cpu().numpy(), x, dims)
+    assert est < 1e-9, est
+    lat.close()
+
+
 def test_asqtad_48x144(dirac):
     dims = (48, 48, 48, 144)
     fat, lng = synth.asqtad_links(dims, 3001, 3002, device="cuda")
