@@ -316,6 +316,13 @@ int dirac_ptc_train(dirac_ptc* net, const void* const* r, const void* const* v, 
  * outer GCR absorbs); on = 0 (default): the FP32 CUDA-core layers used for training. A
  * tensor-core wait that gives up makes the next apply return DIRAC_ERR_TIMEOUT. */
 int dirac_ptc_set_tensor_cores(dirac_ptc* net, int on);
+/* Failure detection tests only (no counterpart in the paper). Every wait of the
+ * tensor-core pipeline has a time budget, wait_seconds (default 2 s); with stall = 1 the
+ * warp that issues the tensor-core instructions stops after loading the weights, as if
+ * it had died, so the other warps' waits run out: the kernel records the error, frees its
+ * tensor memory and returns, and the next dirac_ptc_apply returns DIRAC_ERR_TIMEOUT
+ * (dirac_ptc_set_tensor_cores clears the error). stall = 0 restores normal operation. */
+int dirac_ptc_test_stall(dirac_ptc* net, int stall, double wait_seconds);
 /* Make net the preconditioner of DIRAC_SOLVER_GCR_PTC on ctx (NULL detaches). With
  * force = 0, every such solve starts by applying both the network and the Schwarz
  * preconditioner to the initial residual r0 and keeps the one with the smaller

@@ -151,7 +151,7 @@ void ptc_release(dirac_ptc* n);
 size_t ptc_tc_image_bytes(int cin, int cout);
 void ptc_tc_pack(int cin, int cout, const float2* w, void* img, cudaStream_t st);
 int ptc_tc_layer(int cin, int cout, int recon, const char* const* in, char* const* out, const char* gauge,
-                 const void* img, const Geom& g, int* err, cudaStream_t st);
+                 const void* img, const Geom& g, int* err, uint64_t wait_ns, int stall, cudaStream_t st);
 
 }  // namespace dirac
 

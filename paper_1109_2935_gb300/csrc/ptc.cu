@@ -441,6 +441,8 @@ struct dirac_ptc {
   bool tc_dirty = true;
   int* tc_err_h = nullptr;
   int* tc_err_d = nullptr;
+  uint64_t tc_wait_ns = 2000000000ull;  // budget of each tensor-core pipeline wait
+  int tc_stall = 0;                     // failure tests: the MMA warp stops issuing
 };
 
 namespace dirac {
@@ -611,7 +613,7 @@ int ptc_apply_tc(dirac_ptc* n, char* out, const char* in, cudaStream_t st) {
       a[c] = l == 1 ? in : n->hid + ((size_t)((l - 1) & 1) * MAXC + c) * n->fb;
     for (int c = 0; c < n->ch[l]; ++c) b[c] = l == n->L ? out : n->hid + ((size_t)(l & 1) * MAXC + c) * n->fb;
     int rc = ptc_tc_layer(n->ch[l - 1], n->ch[l], n->c->p.recon[P32], a, b, n->c->gauge[P32], n->tcimg + n->tcoff[l - 1],
-                          geom(n), n->tc_err_d, st);
+                          geom(n), n->tc_err_d, n->tc_wait_ns, n->tc_stall, st);
     if (rc) return net_err(n, rc, "PTC tensor-core layer launch");
   }
   return cuda_check(n->c, "PTC apply (tensor cores)");
@@ -867,6 +869,15 @@ extern "C" int dirac_ptc_train(dirac_ptc* n, const void* const* r, const void* c
 extern "C" int dirac_ptc_set_tensor_cores(dirac_ptc* n, int on) {
   if (!n || (on != 0 && on != 1)) return n ? net_err(n, DIRAC_ERR_ARG, "PTC: tensor cores on must be 0 or 1") : DIRAC_ERR_ARG;
   n->tc = on;
+  *n->tc_err_h = 0;  // a new start after a wait that gave up
+  return DIRAC_OK;
+}
+
+extern "C" int dirac_ptc_test_stall(dirac_ptc* n, int stall, double wait_seconds) {
+  if (!n || (stall != 0 && stall != 1) || !(wait_seconds > 0) || wait_seconds > 60)
+    return n ? net_err(n, DIRAC_ERR_ARG, "PTC test stall: bad arguments") : DIRAC_ERR_ARG;
+  n->tc_stall = stall;
+  n->tc_wait_ns = (uint64_t)(wait_seconds * 1e9);
   return DIRAC_OK;
 }
 

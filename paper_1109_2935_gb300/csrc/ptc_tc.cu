@@ -17,8 +17,8 @@
 // and transports of later paths overlap the MMAs of earlier ones. After the 9 paths each
 // producer warp reads its 32 lanes (= sites) back with tcgen05.ld. B for all paths is
 // copied to shared memory once per CTA by a bulk asynchronous copy (cp.async.bulk).
-// Every wait is bounded; on expiry the kernel records an error in a host-mapped flag,
-// stops issuing, frees its tensor memory and returns.
+// Every wait has a time budget (the global timer); on expiry the kernel records an error
+// in a host-mapped flag, stops issuing, frees its tensor memory and returns.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -31,7 +31,6 @@ namespace {
 
 constexpr int NPATH_TC = 9;
 constexpr int TC_M = 128;
-constexpr unsigned WAIT_LIMIT = 1u << 22;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -69,11 +68,20 @@ __device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
-// true when the phase completed, false when the wait gave up
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-  for (unsigned i = 0; i < WAIT_LIMIT; ++i)
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// true when the phase completed, false when the wait gave up after limit_ns
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint64_t limit_ns) {
+  if (mbar_try(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  for (;;) {
     if (mbar_try(bar, parity)) return true;
-  return false;
+    if (global_ns() - t0 > limit_ns) return false;
+  }
 }
 
 template <int N>
@@ -153,6 +161,8 @@ __global__ void ptc_tc_pack_weights(const float2* w, __nv_bfloat16* img) {
 }
 
 struct TcArg {
+  uint64_t wait_ns;    // budget of every wait (a pipeline step takes microseconds)
+  int stall;           // failure tests only: the MMA warp stops after loading the weights
   const char* in[4];   // input channels (FP32 full fields)
   char* out[4];        // output channels
   const char* gauge;   // FP32 links
@@ -364,7 +374,7 @@ __global__ void __launch_bounds__(TcWarps<CIN>::THREADS, 1) ptc_tc_layer_kernel(
         }
         __syncwarp();  // the site's link, fetched by its first thread, is visible to the others
         const uint32_t st = it % TC_STAGES, ph = (it / TC_STAGES) & 1u;
-        const bool late = !mbar_wait(&empty[st], ph ^ 1u);
+        const bool late = !mbar_wait(&empty[st], ph ^ 1u, a.wait_ns);
         if (__any_sync(0xffffffffu, late || abort_s != 0)) {
           abort_s = 1;
           asm volatile("cp.async.wait_group 0;");
@@ -434,7 +444,7 @@ __global__ void __launch_bounds__(TcWarps<CIN>::THREADS, 1) ptc_tc_layer_kernel(
       // the tile's results: warp w reads lane quarter w % 4 (sites 32 (w % 4) + lane) and
       // stores the output channels co = w / 4 (mod TPS)
       const uint32_t b = tcount & 1u, pb = (tcount >> 1) & 1u;
-      const bool late = !mbar_wait(&accf[b], pb);
+      const bool late = !mbar_wait(&accf[b], pb, a.wait_ns);
       if (__any_sync(0xffffffffu, late || abort_s != 0)) {
         abort_s = 1;
         break;
@@ -507,18 +517,19 @@ __global__ void __launch_bounds__(TcWarps<CIN>::THREADS, 1) ptc_tc_layer_kernel(
       asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
                        smem_u32(Bs)),
                    "l"(a.wimg), "r"(bytes), "r"(smem_u32(&wbar)));
-      if (!mbar_wait(&wbar, 0)) abort_s = 1;
+      if (!mbar_wait(&wbar, 0, a.wait_ns)) abort_s = 1;
     }
     constexpr uint32_t IDESC = instr_desc<S::N>();
     uint32_t it = 0, tcount = 0;
-    for (int tile = blockIdx.x; tile < a.ntiles && !abort_s; tile += gridDim.x, ++tcount) {
+    // a.stall: this warp issues nothing, as if it had died; the producers' waits run out
+    for (int tile = blockIdx.x; tile < a.ntiles && !abort_s && !a.stall; tile += gridDim.x, ++tcount) {
       const uint32_t b = tcount & 1u, pb = (tcount >> 1) & 1u;
-      if (!mbar_wait(&acce[b], pb ^ 1u)) { abort_s = 1; break; }
+      if (!mbar_wait(&acce[b], pb ^ 1u, a.wait_ns)) { abort_s = 1; break; }
       asm volatile("tcgen05.fence::after_thread_sync;");
       const uint32_t dcol = tmem + b * PP::ACC_COLS;
       for (int p = 0; p < NPATH_TC; ++p, ++it) {
         const uint32_t st = it % TC_STAGES, ph = (it / TC_STAGES) & 1u;
-        if (!mbar_wait(&full[st], ph)) { abort_s = 1; break; }
+        if (!mbar_wait(&full[st], ph, a.wait_ns)) { abort_s = 1; break; }
         asm volatile("tcgen05.fence::after_thread_sync;");
         const uint32_t sbase = smem_u32(As + (size_t)st * PP::STAGE_BYTES);
         const uint32_t bbase = smem_u32(Bs + (size_t)p * S::B_BYTES);
@@ -537,7 +548,7 @@ __global__ void __launch_bounds__(TcWarps<CIN>::THREADS, 1) ptc_tc_layer_kernel(
     }
     // every MMA issued here has finished before the tensor memory is freed
     mma_commit(&dbar);
-    if (!mbar_wait(&dbar, 0)) abort_s = 1;
+    if (!mbar_wait(&dbar, 0, a.wait_ns)) abort_s = 1;
   }
   if (abort_s && tid == 0) *(volatile int*)a.err = 1;
   asm volatile("tcgen05.fence::before_thread_sync;");
@@ -620,8 +631,10 @@ void ptc_tc_pack(int cin, int cout, const float2* w, void* img, cudaStream_t st)
 }
 
 int ptc_tc_layer(int cin, int cout, int recon, const char* const* in, char* const* out, const char* gauge,
-                 const void* img, const Geom& g, int* err, cudaStream_t st) {
+                 const void* img, const Geom& g, int* err, uint64_t wait_ns, int stall, cudaStream_t st) {
   TcArg a{};
+  a.wait_ns = wait_ns;
+  a.stall = stall;
   for (int c = 0; c < cin; ++c) a.in[c] = in[c];
   for (int c = 0; c < cout; ++c) a.out[c] = out[c];
   a.gauge = gauge;

@@ -112,6 +112,7 @@ _SIGS = {
                               ctypes.POINTER(PtcTrainParams), _pd, _vp]),
     "dirac_ptc_attach": (_ci, [_vp, _vp, _ci]),
     "dirac_ptc_set_tensor_cores": (_ci, [_vp, _ci]),
+    "dirac_ptc_test_stall": (_ci, [_vp, _ci, _cd]),
     "dirac_ptc_destroy": (_ci, [_vp]),
     "dirac_dd_create": (_ci, [_vp, _ci, _ci, ctypes.POINTER(_vp)]),
     "dirac_dd_scatter": (_ci, [_vp, _vp, _vp]),

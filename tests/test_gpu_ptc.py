@@ -311,3 +311,35 @@ def test_gcr_ptc_without_network_and_bad_arguments(dirac):
     # the context frees networks it still holds
     lat.close()
     net.close()
+
+
+def test_tensor_core_wait_budget_reports_timeout(dirac):
+    """Failure detection without a fault: with the MMA-issuing warp stopped (test stall),
+    the producer warps' waits run out after their 50 ms budget, the kernel frees its tensor
+    memory and returns, the next apply reports ERR_TIMEOUT, and after clearing, the same
+    context and network give the normal result again."""
+    import time
+    dims = (8, 8, 8, 8)
+    lat, U = _lattice(dirac, dims)
+    net = dirac.Ptc(lat, (1, 2, 1))
+    net.set_weights([w.numpy() for w in synth.ptc_weights((1, 2, 1), 8)])
+    net.tensor_cores(True)
+    fin = lat.to_device(synth.wilson_spinor(dims, 40).cuda(), F32)
+    ref = lat.new_field(F32)
+    net.apply(ref, fin)
+    torch.cuda.synchronize()
+    assert dirac.dirac_ptc_test_stall(net.net, 1, 0.05) == dirac.OK
+    out = lat.new_field(F32)
+    t0 = time.time()
+    net.apply(out, fin)           # launches; the kernels give up and return
+    torch.cuda.synchronize()
+    assert time.time() - t0 < 10.0
+    stream = torch.cuda.current_stream().cuda_stream
+    assert dirac.dirac_ptc_apply(net.net, out.data_ptr(), fin.data_ptr(), stream) == dirac.ERR_TIMEOUT
+    assert dirac.dirac_ptc_test_stall(net.net, 0, 2.0) == dirac.OK
+    net.tensor_cores(True)        # clears the recorded error
+    again = lat.new_field(F32)
+    net.apply(again, fin)
+    torch.cuda.synchronize()
+    assert torch.equal(again, ref)
+    assert dirac.dirac_ptc_test_stall(net.net, 1, 0.0) == dirac.ERR_ARG
