@@ -167,7 +167,7 @@ class OracleSample:
     def step(self):
         from oracle import wilson
         t0 = time.perf_counter()
-        wilson.apply_M(self.U, self.A, KAPPA, self.psi, True, sites=self.sites)
+        self.out = wilson.apply_M(self.U, self.A, KAPPA, self.psi, True, sites=self.sites)
         return time.perf_counter() - t0
 
 
@@ -314,6 +314,17 @@ def main():
         cpu = {"value": round(gbs, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
                "sample": f"FP64 numpy oracle, M at {orc.n} fixed random sites of 24^3x128, "
                          f"3 applications ({sum(ts):.2f} s), FP64 1536 B/site count"}
+        # the headline kernel against the oracle at the same sites (one more launch)
+        xh, yh = fields[HEADLINE]
+        lat.apply(yh, xh, -1, PREC_ID[HEADLINE], stream)
+        got = lat.to_natural(yh, PREC_ID[HEADLINE], device="cpu").numpy()
+        s_ = orc.sites
+        got = got[s_[:, 3], s_[:, 2], s_[:, 1], s_[:, 0]].reshape(len(s_), -1)
+        ref = orc.out.reshape(len(s_), -1)
+        import numpy as np
+        err = float(np.max(np.linalg.norm(got - ref, axis=1) / np.linalg.norm(ref, axis=1)))
+        cpu["parity_headline"] = {"sites": orc.n, "max_site_rel_err": float(f"{err:.3e}"),
+                                  "bound": 1e-5, "ok": bool(err <= 1e-5)}
     workload = "wilson-clover %dx%dx%dx%d csw=1.0 kappa=0.135 sigma=0.5 smear=3" % dims
     del fields
     lat.close()
