@@ -338,7 +338,7 @@ static int spinor_xfer(dirac_ctx* c, bool import, void* dev, dirac_prec prec, di
   // tables, any host memory) is read and written in place over the host link by
   // coalesced conversion kernels (FP64 / FP32 storage): no staging copy, one pass.
   bool direct = false;
-  if (!nat_on_device && prec != P16) {
+  if (!nat_on_device && (int)prec != P16) {
     cudaPointerAttributes pa{};
     if (cudaPointerGetAttributes(&pa, nat_ptr) == cudaSuccess && pa.type == cudaMemoryTypeHost && pa.devicePointer) {
       d = (double*)pa.devicePointer;

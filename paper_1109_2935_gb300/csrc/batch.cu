@@ -193,8 +193,8 @@ int dirac_apply_multi(dirac_ctx* c, void* out, const void* in, int nrhs, dirac_p
   const int per_sm = kMaxRG / RG;  // 16 resident warps per SM at the 128-register cap
   const int grid = grid_for(per_sm, L.tiles);
   cudaStream_t st = (cudaStream_t)stream;
-  if (prec == P64) launch_mrhs_prec<P64>(c->p.recon[prec], L, RG, grid, st);
-  else if (prec == P32) launch_mrhs_prec<P32>(c->p.recon[prec], L, RG, grid, st);
+  if ((int)prec == P64) launch_mrhs_prec<P64>(c->p.recon[prec], L, RG, grid, st);
+  else if ((int)prec == P32) launch_mrhs_prec<P32>(c->p.recon[prec], L, RG, grid, st);
   else launch_mrhs_prec<P16>(c->p.recon[prec], L, RG, grid, st);
   return cuda_check(c, "multi-RHS kernel");
 }

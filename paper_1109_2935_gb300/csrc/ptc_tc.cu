@@ -88,21 +88,6 @@ template <int N>
 __device__ __forceinline__ void tmem_ld(uint32_t taddr, float* v);
 
 template <>
-__device__ __forceinline__ void tmem_ld<32>(uint32_t taddr, float* v) {
-  uint32_t r[32];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-      : "r"(taddr));
-#pragma unroll
-  for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
-}
-
-template <>
 __device__ __forceinline__ void tmem_ld<16>(uint32_t taddr, float* v) {
   uint32_t r[16];
   asm volatile(
@@ -132,7 +117,6 @@ struct TcShape {
   static constexpr int N = 2 * NH;                    // 16 or 32
   static constexpr int A_BYTES = TC_M * KC * 2;       // one colour, one path
   static constexpr int B_BYTES = N * KC * 2;          // one path
-  static constexpr int SMEM = NPATH_TC * B_BYTES + 2 * 3 * A_BYTES;
 };
 
 // byte offset of element (row, k) in a K-major no-swizzle tile with KC columns
