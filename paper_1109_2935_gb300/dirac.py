@@ -441,6 +441,32 @@ class Ptc:
     def detach(self):
         return self.lat.check(dirac_ptc_attach(self.lat.ctx, None, 0), "dirac_ptc_attach")
 
+    def save(self, prefix, meta=None):
+        """Checkpoint: the weights as raw little-endian FP64 (re, im) pairs in layer order
+        ([p][c_out][c_in][s][t], the C ABI order) to prefix.bin, and prefix.json with the
+        channel list, the weight count and `meta` (e.g. kappa, lattice, training run)."""
+        import json
+        import numpy as np
+        flat = np.concatenate([w.reshape(-1) for w in self.get_weights()]).astype("<c16")
+        flat.view("<f8").tofile(prefix + ".bin")
+        with open(prefix + ".json", "w") as f:
+            json.dump({"format": "ptc-weights-v1", "channels": list(self.channels), "complex_weights": int(self.n),
+                       "dtype": "float64 little-endian (re, im) pairs", "meta": meta or {}}, f, indent=1)
+
+    def load(self, prefix):
+        """Restore weights saved by save(); the channel lists must match."""
+        import json
+        import numpy as np
+        with open(prefix + ".json") as f:
+            info = json.load(f)
+        if tuple(info["channels"]) != self.channels or info["complex_weights"] != self.n:
+            raise ValueError(f"checkpoint is for channels {info['channels']}, this network has {self.channels}")
+        flat = np.fromfile(prefix + ".bin", dtype="<f8").view(np.complex128)
+        if flat.size != self.n:
+            raise ValueError("checkpoint size does not match its description")
+        self.set_weights(self._split(flat))
+        return info.get("meta", {})
+
     def close(self):
         if self.net and self.lat.ctx:
             dirac_ptc_destroy(self.net)

@@ -343,3 +343,27 @@ def test_tensor_core_wait_budget_reports_timeout(dirac):
     torch.cuda.synchronize()
     assert torch.equal(again, ref)
     assert dirac.dirac_ptc_test_stall(net.net, 1, 0.0) == dirac.ERR_ARG
+
+
+def test_checkpoint_round_trip(dirac, tmp_path):
+    """Weights saved as plain binary + JSON and loaded into a new network on another
+    context give the same weights and the same application, bit for bit."""
+    dims = (4, 4, 4, 8)
+    lat, U = _lattice(dirac, dims)
+    net = dirac.Ptc(lat, (1, 2, 2, 1))
+    net.set_weights(_weights((1, 2, 2, 1), 31, 0.2))
+    prefix = str(tmp_path / "ptc")
+    net.save(prefix, meta={"kappa": 0.12, "dims": list(dims)})
+    lat2, _ = _lattice(dirac, dims)
+    net2 = dirac.Ptc(lat2, (1, 2, 2, 1))
+    assert net2.load(prefix) == {"kappa": 0.12, "dims": list(dims)}
+    for a, b in zip(net.get_weights(), net2.get_weights()):
+        assert np.array_equal(a, b)
+    r = synth.wilson_spinor(dims, 32)
+    o1, o2 = lat.new_field(F32), lat2.new_field(F32)
+    net.apply(o1, lat.to_device(r.cuda(), F32))
+    net2.apply(o2, lat2.to_device(r.cuda(), F32))
+    torch.cuda.synchronize()
+    assert torch.equal(o1, o2)
+    with pytest.raises(ValueError):
+        dirac.Ptc(lat2, (1, 2, 1)).load(prefix)
