@@ -16,11 +16,19 @@
 #include <complex>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "internal.h"
 
 namespace dirac {
 
 using cplx = std::complex<double>;
+
+// NVTX range for a solver phase (host timeline of profilers; no cost without one)
+struct Range {
+  explicit Range(const char* name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
+};
 
 namespace {
 
@@ -43,10 +51,10 @@ enum : int {
   S_MSAB = S_MSSH + KSH,            // a_{k-1}, b_{k-1} of the base system
   S_END = S_MSAB + 4
 };
-enum : int { F_OK = 0, F_BREAKDOWN = 1, F_NONFINITE = 2 };
+enum : int { FLAG_OK = 0, FLAG_BREAKDOWN = 1, FLAG_NONFINITE = 2 };
 
 __device__ __forceinline__ bool bad(double v) { return !isfinite(v); }
-__device__ __forceinline__ void flag(double* S, int f) { if (S[S_FLAG] == F_OK) S[S_FLAG] = f; }
+__device__ __forceinline__ void flag(double* S, int f) { if (S[S_FLAG] == FLAG_OK) S[S_FLAG] = f; }
 __device__ __forceinline__ void cdiv(double ar, double ai, double br, double bi, double& qr, double& qi) {
   double d = br * br + bi * bi;
   qr = (ar * br + ai * bi) / d;
@@ -69,9 +77,9 @@ __global__ void k_mirror(const double* S, int slot, double* mirror, int which, i
 // BiCGstab: beta = (rho/rho_old)(alpha/omega); coefficient -beta*omega
 __global__ void k_bicg1(double* S) {
   double q1r, q1i, q2r, q2i;
-  if (S[S_RHOOLD] == 0 && S[S_RHOOLD + 1] == 0) { flag(S, F_BREAKDOWN); }
-  if (S[S_OMEGA] == 0 && S[S_OMEGA + 1] == 0) { flag(S, F_BREAKDOWN); }
-  if (S[S_FLAG] != F_OK) {
+  if (S[S_RHOOLD] == 0 && S[S_RHOOLD + 1] == 0) { flag(S, FLAG_BREAKDOWN); }
+  if (S[S_OMEGA] == 0 && S[S_OMEGA + 1] == 0) { flag(S, FLAG_BREAKDOWN); }
+  if (S[S_FLAG] != FLAG_OK) {
     S[S_BETA] = S[S_BETA + 1] = S[S_NBW] = S[S_NBW + 1] = 0;
     return;
   }
@@ -85,28 +93,28 @@ __global__ void k_bicg1(double* S) {
 // alpha = rho / (r0, v)
 __global__ void k_bicg2(double* S) {
   double sr = S[S_SIGMA], si = S[S_SIGMA + 1];
-  if (bad(sr) || bad(si)) flag(S, F_NONFINITE);
-  else if (sr == 0 && si == 0) flag(S, F_BREAKDOWN);
+  if (bad(sr) || bad(si)) flag(S, FLAG_NONFINITE);
+  else if (sr == 0 && si == 0) flag(S, FLAG_BREAKDOWN);
   double ar = 0, ai = 0;
-  if (S[S_FLAG] == F_OK) cdiv(S[S_RHO], S[S_RHO + 1], sr, si, ar, ai);
+  if (S[S_FLAG] == FLAG_OK) cdiv(S[S_RHO], S[S_RHO + 1], sr, si, ar, ai);
   S[S_ALPHA] = ar; S[S_ALPHA + 1] = ai;
   S[S_NALPHA] = -ar; S[S_NALPHA + 1] = -ai;
 }
 // omega = (t, s) / (t, t)
 __global__ void k_bicg3(double* S) {
   double tt = S[S_TS + 2];
-  if (bad(tt) || bad(S[S_TS]) || bad(S[S_TS + 1])) flag(S, F_NONFINITE);
-  else if (tt == 0) flag(S, F_BREAKDOWN);
+  if (bad(tt) || bad(S[S_TS]) || bad(S[S_TS + 1])) flag(S, FLAG_NONFINITE);
+  else if (tt == 0) flag(S, FLAG_BREAKDOWN);
   double wr = 0, wi = 0;
-  if (S[S_FLAG] == F_OK) { wr = S[S_TS] / tt; wi = S[S_TS + 1] / tt; }
-  S[S_OMEGA] = S[S_FLAG] == F_OK ? wr : 1; S[S_OMEGA + 1] = S[S_FLAG] == F_OK ? wi : 0;
+  if (S[S_FLAG] == FLAG_OK) { wr = S[S_TS] / tt; wi = S[S_TS + 1] / tt; }
+  S[S_OMEGA] = S[S_FLAG] == FLAG_OK ? wr : 1; S[S_OMEGA + 1] = S[S_FLAG] == FLAG_OK ? wi : 0;
   S[S_NOMEGA] = -wr; S[S_NOMEGA + 1] = -wi;
 }
 // rho_old = rho; rho = (r0, r)
 __global__ void k_bicg4(double* S, double* mirror, int which, int it) {
   S[S_RHOOLD] = S[S_RHO]; S[S_RHOOLD + 1] = S[S_RHO + 1];
   S[S_RHO] = S[S_RN + 1]; S[S_RHO + 1] = S[S_RN + 2];
-  if (bad(S[S_RN])) flag(S, F_NONFINITE);
+  if (bad(S[S_RN])) flag(S, FLAG_NONFINITE);
   mirror[4 * which + 0] = S[S_RN];
   mirror[4 * which + 1] = S[S_FLAG];
   mirror[4 * which + 2] = it;
@@ -117,19 +125,19 @@ __global__ void k_bicg_rho(double* S) { S[S_RHO] = S[S_TMP]; S[S_RHO + 1] = S[S_
 // CG: alpha = rr / (p, Ap)
 __global__ void k_cg1(double* S) {
   double pap = S[S_PAP];
-  if (bad(pap)) flag(S, F_NONFINITE);
-  else if (pap <= 0) flag(S, F_BREAKDOWN);
-  double a = S[S_FLAG] == F_OK ? S[S_RR] / pap : 0;
+  if (bad(pap)) flag(S, FLAG_NONFINITE);
+  else if (pap <= 0) flag(S, FLAG_BREAKDOWN);
+  double a = S[S_FLAG] == FLAG_OK ? S[S_RR] / pap : 0;
   S[S_ALPHA] = a; S[S_ALPHA + 1] = 0;
   S[S_NALPHA] = -a; S[S_NALPHA + 1] = 0;
 }
 // beta = rr_new / rr
 __global__ void k_cg2(double* S, double* mirror, int which, int it) {
   double rn = S[S_RN];
-  if (bad(rn)) flag(S, F_NONFINITE);
-  double b = (S[S_FLAG] == F_OK && S[S_RR] > 0) ? rn / S[S_RR] : 0;
+  if (bad(rn)) flag(S, FLAG_NONFINITE);
+  double b = (S[S_FLAG] == FLAG_OK && S[S_RR] > 0) ? rn / S[S_RR] : 0;
   S[S_BETA] = b; S[S_BETA + 1] = 0;
-  if (S[S_FLAG] == F_OK) S[S_RR] = rn;
+  if (S[S_FLAG] == FLAG_OK) S[S_RR] = rn;
   mirror[4 * which + 0] = rn;
   mirror[4 * which + 1] = S[S_FLAG];
   mirror[4 * which + 2] = it;
@@ -138,11 +146,11 @@ __global__ void k_cg2(double* S, double* mirror, int which, int it) {
 // GCR: gamma_k = ||z_k||, 1/gamma_k; move beta_{0,k} (a cdot result) into its slot
 __global__ void k_gcr_gamma(double* S, int k) {
   double zz = S[S_ZZ];
-  if (bad(zz)) flag(S, F_NONFINITE);
-  else if (zz <= 0) flag(S, F_BREAKDOWN);
-  double g = S[S_FLAG] == F_OK ? sqrt(zz) : 1;
+  if (bad(zz)) flag(S, FLAG_NONFINITE);
+  else if (zz <= 0) flag(S, FLAG_BREAKDOWN);
+  double g = S[S_FLAG] == FLAG_OK ? sqrt(zz) : 1;
   S[S_GG + 4 * k] = g;
-  S[S_INVG] = S[S_FLAG] == F_OK ? 1.0 / g : 0;
+  S[S_INVG] = S[S_FLAG] == FLAG_OK ? 1.0 / g : 0;
   S[S_INVG + 1] = 0;
   if (k > 0) {
     S[S_GB + 4 * (0 * KMAX + k) + 1] = S[S_B0];
@@ -191,17 +199,17 @@ __global__ void k_ms_init(double* S, int n, ShiftTable sh) {
 // base system: alpha = rr / (p, (A + sigma_0) p)
 __global__ void k_ms1(double* S) {
   double pap = S[S_PAP];
-  if (bad(pap)) flag(S, F_NONFINITE);
-  else if (pap <= 0) flag(S, F_BREAKDOWN);
-  double a = S[S_FLAG] == F_OK ? S[S_RR] / pap : 0;
+  if (bad(pap)) flag(S, FLAG_NONFINITE);
+  else if (pap <= 0) flag(S, FLAG_BREAKDOWN);
+  double a = S[S_FLAG] == FLAG_OK ? S[S_RR] / pap : 0;
   S[S_ALPHA] = a;
   S[S_NALPHA] = -a; S[S_NALPHA + 1] = 0;
 }
 // every shift: zeta_{k+1}, a_j, b_j; retire systems that converged last time
 __global__ void k_ms2(double* S, int n, int j0, double tol2bb, double* mirror, int which, int it) {
   const double a = S[S_ALPHA], rr = S[S_RR], rn = S[S_RN];
-  if (bad(rn)) flag(S, F_NONFINITE);
-  const double bk = (S[S_FLAG] == F_OK && rr > 0) ? rn / rr : 0;
+  if (bad(rn)) flag(S, FLAG_NONFINITE);
+  const double bk = (S[S_FLAG] == FLAG_OK && rr > 0) ? rn / rr : 0;
   const double ap = S[S_MSAB], bp = S[S_MSAB + 1], s0 = S[S_MSSH + j0];
   double worst = 0;
   int nact = 0;
@@ -216,7 +224,7 @@ __global__ void k_ms2(double* S, int n, int j0, double tol2bb, double* mirror, i
       zn = den != 0 ? z * zp * ap / den : 0;
     }
     if (bad(zn) || z == 0) {
-      flag(S, F_NONFINITE);
+      flag(S, FLAG_NONFINITE);
       S[S_MSC + 4 * j + 3] = 0;
       continue;
     }
@@ -234,7 +242,7 @@ __global__ void k_ms2(double* S, int n, int j0, double tol2bb, double* mirror, i
   }
   S[S_MSAB] = a;
   S[S_MSAB + 1] = bk;
-  if (S[S_FLAG] == F_OK) S[S_RR] = rn;
+  if (S[S_FLAG] == FLAG_OK) S[S_RR] = rn;
   mirror[4 * which + 0] = worst;
   mirror[4 * which + 1] = S[S_FLAG];
   mirror[4 * which + 2] = it;
@@ -313,7 +321,7 @@ int blas_fail(Ctx& S, int rc) {
 bool finite(double v) { return std::isfinite(v); }
 
 int flag_error(Ctx& S, int fl, const char* who) {
-  if (fl == F_BREAKDOWN) return set_err(S.c, DIRAC_ERR_BREAKDOWN, std::string(who) + ": a Krylov denominator vanished");
+  if (fl == FLAG_BREAKDOWN) return set_err(S.c, DIRAC_ERR_BREAKDOWN, std::string(who) + ": a Krylov denominator vanished");
   return set_err(S.c, DIRAC_ERR_NONFINITE, std::string(who) + ": non-finite scalar");
 }
 
@@ -324,6 +332,7 @@ int accum_prec(int sp) { return sp == P16 ? P32 : sp; }
 
 // r = b - A x in FP64, returns ||r||^2 (host, synchronising)
 int true_residual(Ctx& S, char* r, const char* x, const char* b, double* rr) {
+  Range range("true residual (FP64)");
   TRY(S.A(r, x, P64));
   BT(blas_xmy_norm(S.c->blas, S.f(b, P64), S.f(r, P64), rr, S.st));
   return DIRAC_OK;
@@ -377,7 +386,7 @@ int solve_cg(Ctx& S, char* x, const char* b, const dirac_solver_params& P) {
       double rp;
       int fl;
       TRY(S.read(it - 1, &rp, &fl));
-      if (fl != F_OK) return flag_error(S, fl, "CG");
+      if (fl != FLAG_OK) return flag_error(S, fl, "CG");
       if ((d2 > 0 && rp < d2 * rmax) || rp < target) {
         // reliable update: fold the sloppy correction into x, recompute r in FP64
         BT(blas_axpby(B, cval(1), S.f(xs, ap), cval(1), S.f(x, P64), S.st));
@@ -482,6 +491,7 @@ int solve_bicgstab(Ctx& S, char* x, const char* b, const dirac_solver_params& P)
   bool converged = false;
   // one iteration; its launches depend only on the mirror slot it & 1
   auto step = [&](int slot) -> int {
+    Range range("BiCGstab iteration");
     KC((k_bicg1<<<1, 1, 0, S.st>>>(S.S)));
     // p = r + beta (p - omega v)
     BT(blas_pupdate(B, S.f(rs, sp), cptr(S.slot(S_BETA)), cptr(S.slot(S_NBW)), S.f(v, sp), S.f(p, sp), S.st));
@@ -509,7 +519,7 @@ int solve_bicgstab(Ctx& S, char* x, const char* b, const dirac_solver_params& P)
       double rp;
       int fl;
       TRY(S.read(it - 1, &rp, &fl));
-      if (fl != F_OK) return flag_error(S, fl, "BiCGstab");
+      if (fl != FLAG_OK) return flag_error(S, fl, "BiCGstab");
       if ((d2 > 0 && rp < d2 * rmax) || rp < target) {
         BT(blas_axpby(B, cval(1), S.f(xs, ap), cval(1), S.f(x, P64), S.st));
         BT(blas_zero(B, S.f(xs, ap), S.st));
@@ -542,6 +552,7 @@ struct Precond {
 };
 
 int precond_apply(Ctx& S, Precond& K, int kind, char* out, const char* in, int sp, int pp) {
+  Range range(kind == K_PTC ? "preconditioner (PTC)" : "preconditioner (Schwarz)");
   Blas* B = S.c->blas;
   const int kp = kind == K_PTC ? P32 : pp;
   S.stats->precond_calls++;
@@ -618,6 +629,7 @@ int solve_gcr(Ctx& S, char* x, const char* b, const dirac_solver_params& P, int 
   // residual update. Its launches depend only on k, so from the second restart cycle on
   // each step replays a CUDA graph captured the cycle before.
   auto step = [&](int k) -> int {
+    Range range("GCR step");
     // p_k = K r_k
     if (kind != K_NONE) {
       TRY(precond_apply(S, K, kind, pv[k], rh, sp, pp));
@@ -660,14 +672,14 @@ int solve_gcr(Ctx& S, char* x, const char* b, const dirac_solver_params& P, int 
       double rp;
       int fl;
       TRY(S.read(k - 2, &rp, &fl));
-      if (fl != F_OK) return flag_error(S, fl, "GCR");
+      if (fl != FLAG_OK) return flag_error(S, fl, "GCR");
       restart = (d2 > 0 && rp < d2 * r0n2) || rp < target;
     }
     if (restart) {
       double rp;
       int fl;
       TRY(S.read(k - 1, &rp, &fl));
-      if (fl != F_OK) return flag_error(S, fl, "GCR");
+      if (fl != FLAG_OK) return flag_error(S, fl, "GCR");
       KC((k_gcr_backsub<<<1, 1, 0, S.st>>>(S.S, k)));
       std::vector<Cf> cf(k);
       std::vector<FieldRef> xs(k);
@@ -740,7 +752,7 @@ int solve_ms_stage(Ctx& S, char* const* xout, const char* b, const double* shift
       double worst;
       int fl;
       TRY(S.read(it - 1, &worst, &fl));
-      if (fl != F_OK) return flag_error(S, fl, "multi-shift CG");
+      if (fl != FLAG_OK) return flag_error(S, fl, "multi-shift CG");
       if (S.hmirror[4 * ((it - 1) & 1) + 3] == 0) break;  // every shift converged
     }
     ++it;
@@ -749,7 +761,7 @@ int solve_ms_stage(Ctx& S, char* const* xout, const char* b, const double* shift
     double worst;
     int fl;
     TRY(S.read(last, &worst, &fl));
-    if (fl != F_OK) return flag_error(S, fl, "multi-shift CG");
+    if (fl != FLAG_OK) return flag_error(S, fl, "multi-shift CG");
   }
   for (int j = 0; j < n; ++j) BT(blas_copy(B, S.f(xout[j], P64), xs[j], S.st));
   return DIRAC_OK;
@@ -873,6 +885,7 @@ extern "C" int solve_multishift(dirac_ctx* c, void* const* x, const void* b, con
 
 extern "C" int solve(dirac_ctx* c, void* x, const void* b, const dirac_solver_params* params,
                      dirac_solver_stats* stats, void* stream) {
+  Range range("solve");
   if (!c || !x || !b || !params || x == b) return set_err(c, DIRAC_ERR_ARG, "bad solve arguments");
   const dirac_solver_params& P = *params;
   const bool wil = c->p.kind == DIRAC_WILSON_CLOVER;

@@ -3,6 +3,7 @@ the oracle recomputes ||b - A x|| / ||b|| from the exported solution, which must
 <= the requested tolerance (1e-10), in pure FP64 and in mixed precision."""
 import numpy as np
 import pytest
+import torch
 
 from helpers import F16, F32, F64
 from oracle import staggered, wilson
@@ -165,3 +166,26 @@ def test_nonfinite_source_is_reported(dirac, alg):
     st = lat.solve(fx, fb, getattr(dirac, alg), tol=1e-10, max_iter=50, prec_sloppy=F32,
                    prec_precond=F32, raise_on_error=False)
     assert st["status"] == "ERR_NONFINITE", st
+
+
+@pytest.mark.parametrize("alg", ["CG_NORMAL", "BICGSTAB", "GCR"])
+def test_singular_operator_is_reported(dirac, alg):
+    """Free Wilson operator, periodic in t, kappa = 1/8: the constant spinor is an exact
+    zero mode (M 1 = (1 - 8 kappa) 1 = 0), so M x = b has no solution for a generic b.
+    Every solver stops within its budget with a status (not converged or breakdown)
+    instead of returning OK or running on."""
+    dims = (4, 4, 4, 4)
+    lat = dirac.Lattice(dims, dirac.WILSON_CLOVER, kappa=0.125, csw=0.0, t_antiperiodic=False)
+    lat.load_gauge(synth.unit_gauge(dims))
+    # the zero mode exists on the device too
+    one = torch.zeros(dims[::-1] + (4, 3), dtype=torch.complex128)
+    one[..., 0, 0] = 1.0
+    f1 = lat.to_device(one.cuda(), F64)
+    m1 = lat.new_field(F64)
+    lat.apply(m1, f1, dirac.PARITY_FULL, F64)
+    assert lat.norm2(m1, F64) < 1e-28
+    fb = lat.to_device(synth.wilson_spinor(dims, 5).cuda(), F64)
+    fx = lat.new_field(F64)
+    st = lat.solve(fx, fb, getattr(dirac, alg), tol=1e-10, max_iter=300, raise_on_error=False)
+    assert st["status"] in ("ERR_NOT_CONVERGED", "ERR_BREAKDOWN"), st
+    assert st["iters"] <= 300
