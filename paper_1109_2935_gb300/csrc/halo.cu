@@ -168,7 +168,7 @@ struct DDArg {
 
 // M (or M^dagger) at one local site, the operation order of wilson_site<PREC,R,true>.
 template <int PREC, int R>
-__global__ void __launch_bounds__(DD_THREADS) dd_wilson_kernel(const DDArg a) {
+__global__ void __launch_bounds__(WilsonShape<PREC>::threads, WilsonShape<PREC>::minb) dd_wilson_kernel(const DDArg a) {
   using T = typename Real<PREC>::T;
   const Geom& g = a.g;
   const int Vh = g.Vh, F = g.L[0] * g.L[1] * g.L[2];
@@ -260,10 +260,11 @@ void launch_dd(int recon, const DDArg& a, cudaStream_t st) {
   const int F = a.g.L[0] * a.g.L[1] * a.g.L[2];
   const int n = a.nslices * F;
   if (n <= 0) return;
-  dim3 grid((n + DD_THREADS - 1) / DD_THREADS);
-  if (recon == 18) dd_wilson_kernel<PREC, 18><<<grid, DD_THREADS, 0, st>>>(a);
-  else if (recon == 12) dd_wilson_kernel<PREC, 12><<<grid, DD_THREADS, 0, st>>>(a);
-  else dd_wilson_kernel<PREC, 8><<<grid, DD_THREADS, 0, st>>>(a);
+  constexpr int T = WilsonShape<PREC>::threads;  // the single-domain kernel's launch shape
+  dim3 grid((n + T - 1) / T);
+  if (recon == 18) dd_wilson_kernel<PREC, 18><<<grid, T, 0, st>>>(a);
+  else if (recon == 12) dd_wilson_kernel<PREC, 12><<<grid, T, 0, st>>>(a);
+  else dd_wilson_kernel<PREC, 8><<<grid, T, 0, st>>>(a);
 }
 
 void launch_dd_any(int prec, int recon, const DDArg& a, cudaStream_t st) {
