@@ -103,3 +103,48 @@ def test_batch_argument_checks(dirac):
         dirac.Batch([l1, l2], [torch.zeros_like(x1), torch.zeros_like(x2)], [x1, x2], [2, 2], F32)
     # in and out overlapping
     assert dirac.dirac_apply_multi(l1.ctx, x1.data_ptr(), x1.data_ptr(), 2, F32, None) == dirac.ERR_ARG
+
+
+def test_batch_at_the_configured_sizes(dirac):
+    """The benchmark's batched workload: 16^3x32, 24^3x64 and 32^3x64 with 12 right-hand
+    sides each (kappa 0.130 / 0.133 / 0.136, FP16 storage) in one persistent launch: every
+    output equals the single-RHS kernel's bit for bit, and one right-hand side of the
+    largest lattice matches the oracle on sampled sites."""
+    from oracle.lattice import all_coords
+    specs = [((16, 16, 16, 32), 0.130, 4001), ((24, 24, 24, 64), 0.133, 4003), ((32, 32, 32, 64), 0.136, 4005)]
+    nrhs, prec = 12, F16
+    lats, ins, outs, Us = [], [], [], []
+    for dims, kappa, seed in specs:
+        U = synth.wilson_gauge(dims, 0.5, 3, seed, device="cuda")
+        lat = dirac.Lattice(dims, dirac.WILSON_CLOVER, kappa=kappa, csw=1.0, recon=(18, 12, 12))
+        lat.load_gauge(U)
+        fb = lat.field_bytes(prec)
+        xin = torch.zeros(nrhs * fb, dtype=torch.uint8, device="cuda")
+        for r in range(nrhs):
+            lat.import_spinor(xin[r * fb:(r + 1) * fb], prec, -1, synth.wilson_spinor(dims, seed + 1 + 17 * r,
+                                                                                        device="cuda"))
+        lats.append(lat)
+        ins.append(xin)
+        outs.append(torch.zeros_like(xin))
+        Us.append(U)
+    b = dirac.Batch(lats, outs, ins, [nrhs] * 3, prec)
+    b.apply()
+    torch.cuda.synchronize()
+    for lat, xin, out in zip(lats, ins, outs):
+        fb = lat.field_bytes(prec)
+        for r in range(nrhs):
+            ref = lat.new_field(prec)
+            lat.apply(ref, xin[r * fb:(r + 1) * fb], dirac.PARITY_FULL, prec)
+            assert torch.equal(out[r * fb:(r + 1) * fb], ref), (lat.dims, r)
+    # the oracle on sampled sites of the last right-hand side of 32^3x64
+    lat, xin, out, U = lats[-1], ins[-1], outs[-1], Us[-1]
+    dims, kappa = specs[-1][0], specs[-1][1]
+    fb = lat.field_bytes(prec)
+    psi = lat.to_natural(xin[(nrhs - 1) * fb:], prec, device="cpu").numpy()   # decoded FP16 input
+    got = lat.to_natural(out[(nrhs - 1) * fb:], prec, device="cpu").numpy()
+    rng = np.random.default_rng(1)
+    c = all_coords(dims)
+    s = c[rng.choice(len(c), 256, replace=False)]
+    ref = wilson.apply_M_sites(dec_links(U.cpu().numpy(), prec), 1.0, kappa, psi, s, True, False,
+                               Ahat_codec=lambda A: dec_clover_hat(A, prec))
+    check(got[s[:, 3], s[:, 2], s[:, 1], s[:, 0]], ref, prec, 24, "batched 32^3x64 sampled")

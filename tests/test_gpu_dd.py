@@ -97,3 +97,25 @@ def test_dd_repeated_applications_and_bad_partition(dirac):
         dirac.DomainDecomposition(lat, 8, F32)   # LT / 8 = 1 slice
     with pytest.raises(dirac.DiracError):
         dirac.DomainDecomposition(lat, 3, F32)   # 8 / 3 not an integer
+
+
+@pytest.mark.parametrize("prec,nranks", [(F32, 2), (F32, 8), (F64, 4)])
+def test_dd_full_size(dirac, prec, nranks):
+    """24^3x128 (the benchmark lattice): the decomposed operator equals the single-domain
+    one bit for bit."""
+    dims = (24, 24, 24, 128)
+    U = synth.wilson_gauge(dims, 0.5, 3, 2001, device="cuda")
+    lat = dirac.Lattice(dims, dirac.WILSON_CLOVER, kappa=0.135, csw=1.0, recon=(18, 12, 12))
+    lat.load_gauge(U)
+    src = lat.to_device(synth.wilson_spinor(dims, 2002, device="cuda"), prec)
+    ref = lat.new_field(prec)
+    lat.apply(ref, src, prec=prec)
+    dd = dirac.DomainDecomposition(lat, nranks, prec)
+    out = torch.zeros_like(ref)
+    dd.scatter(src)
+    dd.apply()
+    dd.gather(out)
+    torch.cuda.synchronize()
+    assert torch.equal(out, ref)
+    dd.close()
+    lat.close()
