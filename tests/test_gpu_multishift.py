@@ -1,5 +1,5 @@
 """Multi-shift solves of Eq. 4 (Sec. 8.2 strategy: sloppy multi-shift CG, then mixed
-precision refinement per shift), judged by the FP64 oracle: every x_j must satisfy
+precision refinement per shift), checked by the FP64 oracle: every x_j must satisfy
 ||b - (M^dagger M + sigma_j) x_j|| / ||b|| <= 1e-10."""
 import ctypes
 

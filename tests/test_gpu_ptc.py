@@ -1,6 +1,6 @@
 """GPU parity of the parallel-transport convolution (PTC) network (dirac_ptc_*) against
 the FP64 oracle (oracle/ptc.py): forward, loss and weight gradients, one Adam step,
-training, and its use as the preconditioner of flexible GCR judged by the oracle's
+training, and its use as the preconditioner of flexible GCR checked by the oracle's
 true residual. FP32 arithmetic: 1e-5 relative."""
 import numpy as np
 import pytest

@@ -1,4 +1,4 @@
-"""GPU solves (CG, BiCGstab, GCR, GCR-DD of Algorithm 1) judged by the FP64 oracle:
+"""GPU solves (CG, BiCGstab, GCR, GCR-DD of Algorithm 1) checked by the FP64 oracle:
 the oracle recomputes ||b - A x|| / ||b|| from the exported solution, which must be
 <= the requested tolerance (1e-10), in pure FP64 and in mixed precision."""
 import numpy as np
