@@ -10,6 +10,7 @@
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <type_traits>
 
 #include "internal.h"
 
@@ -90,6 +91,48 @@ __device__ __forceinline__ void site_store(const FieldRef& f, int s, const T v[N
     for (int k = 0; k < NR; ++k) t[k] = (float)v[k];
     if (f.prec == P32) SpinorIO<P32, NR>::store(b, f.Vh, cb, t);
     else SpinorIO<P16, NR>::store(b, f.Vh, cb, t);
+  }
+}
+
+// Stores v like site_store and leaves in v the values as stored, so that a reduction
+// over the result needs no reload: for FP16 the binary16 values times the per-site
+// norm, computed exactly as a load decodes them; FP32 / FP64 storage leaves v as it is.
+template <int NR, typename T>
+__device__ __forceinline__ void site_store_q(const FieldRef& f, int s, T v[NR]) {
+  if (f.prec != P16) {
+    site_store<NR>(f, s, v);
+    return;
+  }
+  int q = s >= f.Vh ? 1 : 0;
+  int cb = s - q * f.Vh;
+  char* b = f.p + q * f.hb;
+  float t[NR], inv;
+#pragma unroll
+  for (int k = 0; k < NR; ++k) t[k] = (float)v[k];
+  const float n = site_norm_scale(t, NR, inv);
+  if constexpr (NR == 24) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      float w[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) w[j] = t[8 * k + j] * inv;
+      const int4 h = pack_half8(w);
+      *reinterpret_cast<int4*>(b + ((size_t)k * f.Vh + cb) * 16) = h;
+      unpack_half8(h, w);
+#pragma unroll
+      for (int j = 0; j < 8; ++j) v[8 * k + j] = (T)(w[j] * n);
+    }
+    reinterpret_cast<float*>(b + (size_t)48 * f.Vh)[cb] = n;
+  } else {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const __half2 h = __floats2half2_rn(t[2 * k] * inv, t[2 * k + 1] * inv);
+      *reinterpret_cast<__half2*>(b + ((size_t)k * f.Vh + cb) * 4) = h;
+      const float2 w = __half22float2(h);
+      v[2 * k] = (T)(w.x * n);
+      v[2 * k + 1] = (T)(w.y * n);
+    }
+    reinterpret_cast<float*>(b + (size_t)12 * f.Vh)[cb] = n;
   }
 }
 
@@ -177,14 +220,13 @@ template <int NR, typename T> struct OpCdotNorm {
   }
 };
 template <int NR, typename T>
-__device__ __forceinline__ void acc_norm_dot(const T* v, const FieldRef* w, int i, double* acc, bool dot) {
+__device__ __forceinline__ void acc_norm_dot(const T* v, const T* ww, double* acc) {
   T nn = 0;
 #pragma unroll
   for (int k = 0; k < NR; ++k) nn = fma(v[k], v[k], nn);
   acc[0] += (double)nn;
-  if (dot) {
-    T ww[NR], re = 0, im = 0;
-    site_load<NR>(*w, i, ww);
+  if (ww) {
+    T re = 0, im = 0;
 #pragma unroll
     for (int k = 0; k < NR / 2; ++k) {
       re = fma(ww[2 * k], v[2 * k], re); re = fma(ww[2 * k + 1], v[2 * k + 1], re);
@@ -193,94 +235,110 @@ __device__ __forceinline__ void acc_norm_dot(const T* v, const FieldRef* w, int 
     acc[1] += (double)re; acc[2] += (double)im;
   }
 }
-// y += a x ; ||y||^2, (w, y)
+// y += a x ; ||y||^2, (w, y). Every input is loaded before the store; a w that is y
+// itself means the updated y.
 template <int NR, typename T, bool DOT> struct OpCaxpyNorm {
+  static constexpr int kMinBlocks = sizeof(T) == 4 ? 2 : 1;
   FieldRef x, y, w; Cf a;
   __device__ void operator()(int i, double* acc) const {
     T ar, ai;
     cf_get(a, ar, ai);
-    T u[NR], v[NR];
+    T u[NR], v[NR], ww[DOT ? NR : 1];
     site_load<NR>(x, i, u); site_load<NR>(y, i, v);
+    const bool wy = DOT && w.p == y.p;
+    if constexpr (DOT) if (!wy) site_load<NR>(w, i, ww);
 #pragma unroll
     for (int k = 0; k < NR / 2; ++k) {
       T xr = u[2 * k], xi = u[2 * k + 1];
       v[2 * k] += ar * xr - ai * xi;
       v[2 * k + 1] += ar * xi + ai * xr;
     }
-    site_store<NR>(y, i, v);
-    if (y.prec == P16) site_load<NR>(y, i, v);  // reduce what is stored
-    acc_norm_dot<NR, T>(v, &w, i, acc, DOT);
+    site_store_q<NR>(y, i, v);  // reduce what is stored
+    if constexpr (DOT) {
+      if (wy)
+#pragma unroll
+        for (int k = 0; k < NR; ++k) ww[k] = v[k];
+      acc_norm_dot<NR, T>(v, ww, acc);
+    } else {
+      acc_norm_dot<NR, T>(v, nullptr, acc);
+    }
   }
 };
-// xs += a p + b s ;  s += c t (s becomes r) ; ||r||^2, (w, r)     (BiCGstab)
+// xs += a p + b s ;  s += c t (s becomes r) ; ||r||^2, (w, r)     (BiCGstab; p, s, t
+// and xs are distinct and loaded before the first store, w after the last)
 template <int NR, typename T> struct OpBicgXR {
+  static constexpr int kMinBlocks = sizeof(T) == 4 ? 2 : 1;
   FieldRef p, s, t, xs, w; Cf a, b, c;
   __device__ void operator()(int i, double* acc) const {
     T ar, ai, br, bi, cr, ci;
     cf_get(a, ar, ai);
     cf_get(b, br, bi);
     cf_get(c, cr, ci);
-    T up[NR], us[NR], ux[NR];
+    T up[NR], us[NR], ux[NR], ut[NR];
     site_load<NR>(p, i, up); site_load<NR>(s, i, us); site_load<NR>(xs, i, ux);
+    site_load<NR>(t, i, ut);
 #pragma unroll
     for (int k = 0; k < NR / 2; ++k) {
       ux[2 * k] += ar * up[2 * k] - ai * up[2 * k + 1] + br * us[2 * k] - bi * us[2 * k + 1];
       ux[2 * k + 1] += ar * up[2 * k + 1] + ai * up[2 * k] + br * us[2 * k + 1] + bi * us[2 * k];
     }
     site_store<NR>(xs, i, ux);
-    T ut[NR];
-    site_load<NR>(t, i, ut);
 #pragma unroll
     for (int k = 0; k < NR / 2; ++k) {
       T tr = ut[2 * k], ti = ut[2 * k + 1];
       us[2 * k] += cr * tr - ci * ti;
       us[2 * k + 1] += cr * ti + ci * tr;
     }
-    site_store<NR>(s, i, us);
-    if (s.prec == P16) site_load<NR>(s, i, us);
-    acc_norm_dot<NR, T>(us, &w, i, acc, true);
+    site_store_q<NR>(s, i, us);
+    T ww[NR];
+    site_load<NR>(w, i, ww);
+    acc_norm_dot<NR, T>(us, ww, acc);
   }
 };
-// xs += a p ; r += c Ap ; ||r||^2     (CG, c = -a)
+// xs += a p ; r += c Ap ; ||r||^2     (CG, c = -a; distinct fields, all loaded first)
 template <int NR, typename T> struct OpCgUpdate {
+  static constexpr int kMinBlocks = sizeof(T) == 4 ? 2 : 1;
   FieldRef p, Ap, xs, r; Cf a, c;
   __device__ void operator()(int i, double* acc) const {
     T ar, ai, cr, ci;
     cf_get(a, ar, ai);
     cf_get(c, cr, ci);
-    T up[NR], ux[NR];
+    T up[NR], ux[NR], ua[NR], ur[NR];
     site_load<NR>(p, i, up); site_load<NR>(xs, i, ux);
+    site_load<NR>(Ap, i, ua); site_load<NR>(r, i, ur);
 #pragma unroll
     for (int k = 0; k < NR / 2; ++k) {
       ux[2 * k] += ar * up[2 * k] - ai * up[2 * k + 1];
       ux[2 * k + 1] += ar * up[2 * k + 1] + ai * up[2 * k];
     }
     site_store<NR>(xs, i, ux);
-    T ua[NR], ur[NR];
-    site_load<NR>(Ap, i, ua); site_load<NR>(r, i, ur);
 #pragma unroll
     for (int k = 0; k < NR / 2; ++k) {
       ur[2 * k] += cr * ua[2 * k] - ci * ua[2 * k + 1];
       ur[2 * k + 1] += cr * ua[2 * k + 1] + ci * ua[2 * k];
     }
-    site_store<NR>(r, i, ur);
-    if (r.prec == P16) site_load<NR>(r, i, ur);
-    acc_norm_dot<NR, T>(ur, nullptr, i, acc, false);
+    site_store_q<NR>(r, i, ur);
+    acc_norm_dot<NR, T>(ur, nullptr, acc);
   }
 };
-// x *= s (real part of the coefficient) ; (x, y)
+// x *= s (real part of the coefficient) ; (x, y). y is loaded before the store; a y
+// that is x itself means the scaled x.
 template <int NR, typename T> struct OpScaleCdot {
+  static constexpr int kMinBlocks = sizeof(T) == 4 ? 2 : 1;
   FieldRef x, y; Cf s;
   __device__ void operator()(int i, double* acc) const {
     T sr, si;
     cf_get(s, sr, si);
     T u[NR], v[NR];
+    const bool xy = x.p == y.p;
     site_load<NR>(x, i, u);
+    if (!xy) site_load<NR>(y, i, v);
 #pragma unroll
     for (int k = 0; k < NR; ++k) u[k] *= sr;
-    site_store<NR>(x, i, u);
-    if (x.prec == P16) site_load<NR>(x, i, u);
-    site_load<NR>(y, i, v);
+    site_store_q<NR>(x, i, u);
+    if (xy)
+#pragma unroll
+      for (int k = 0; k < NR; ++k) v[k] = u[k];
     T re = 0, im = 0;
 #pragma unroll
     for (int k = 0; k < NR / 2; ++k) {
@@ -307,22 +365,30 @@ template <int NR, typename T> struct OpXmyNorm {
   }
 };
 struct MultiCoef { FieldRef x[kMaxMulti]; Cf c[kMaxMulti]; int n; };
-template <int NR, typename T> struct OpMultiCaxpy {
+// y += sum_j c_j x_j. The sum is formed in TS (FP32 when no x_j is FP64) and added to
+// y in T, so a GCR restart's FP64 solution update over low-precision directions runs
+// at the FP32 rate.
+template <int NR, typename T, typename TS> struct OpMultiCaxpy {
   MultiCoef m; FieldRef y;
   __device__ void operator()(int i, double*) const {
-    T v[NR];
-    site_load<NR>(y, i, v);
+    TS s[NR];
+#pragma unroll
+    for (int k = 0; k < NR; ++k) s[k] = 0;
     for (int j = 0; j < m.n; ++j) {
-      T u[NR];
+      TS u[NR];
       site_load<NR>(m.x[j], i, u);
-      T cr, ci;
+      TS cr, ci;
       cf_get(m.c[j], cr, ci);
 #pragma unroll
       for (int k = 0; k < NR / 2; ++k) {
-        v[2 * k] += cr * u[2 * k] - ci * u[2 * k + 1];
-        v[2 * k + 1] += cr * u[2 * k + 1] + ci * u[2 * k];
+        s[2 * k] += cr * u[2 * k] - ci * u[2 * k + 1];
+        s[2 * k + 1] += cr * u[2 * k + 1] + ci * u[2 * k];
       }
     }
+    T v[NR];
+    site_load<NR>(y, i, v);
+#pragma unroll
+    for (int k = 0; k < NR; ++k) v[k] += (T)s[k];
     site_store<NR>(y, i, v);
   }
 };
@@ -354,6 +420,13 @@ template <int NR, typename T> struct OpMultiShift {
 };
 
 // ---------------------------------------------------------------- kernels
+// Resident CTAs per SM that an op asks the register allocator for (its kMinBlocks,
+// else 1): the FP32 update-and-reduce ops keep two 256-thread CTAs per SM.
+template <class Op, class = void> struct MinBlocks { static constexpr int value = 1; };
+template <class Op> struct MinBlocks<Op, std::void_t<decltype(Op::kMinBlocks)>> {
+  static constexpr int value = Op::kMinBlocks;
+};
+
 template <class Op>
 __global__ void __launch_bounds__(kThreads) blas_map_kernel(Op op, int n) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) op(i, nullptr);
@@ -385,7 +458,7 @@ __device__ __forceinline__ void block_sum3(double acc[3], double (*sh)[3]) {
 }
 
 template <class Op>
-__global__ void __launch_bounds__(kThreads) blas_reduce_kernel(Op op, int n, double* partials,
+__global__ void __launch_bounds__(kThreads, MinBlocks<Op>::value) blas_reduce_kernel(Op op, int n, double* partials,
                                                           unsigned* ticket, double* res) {
   __shared__ double sh[kThreads / 32][3];
   __shared__ bool last;
@@ -544,14 +617,19 @@ int blas_multi_caxpy(Blas* b, int n, const Cf* c, const FieldRef* xs, const Fiel
   for (int j0 = 0; j0 < n; j0 += kMaxMulti) {
     MultiCoef m;
     m.n = n - j0 < kMaxMulti ? n - j0 : kMaxMulti;
-    bool dbl = y.prec == P64;
+    bool xdbl = false;
     for (int j = 0; j < m.n; ++j) {
       m.x[j] = xs[j0 + j];
       m.c[j] = c[j0 + j];
-      dbl = dbl || xs[j0 + j].prec == P64;
+      xdbl = xdbl || xs[j0 + j].prec == P64;
     }
     int rc;
-    DISPATCH(y.nr, dbl, rc = run_map(b, (OpMultiCaxpy<NR, T>{m, y}), nsites(y), st));
+    if (y.prec == P64 && !xdbl) {
+      if (y.nr == 24) rc = run_map(b, (OpMultiCaxpy<24, double, float>{m, y}), nsites(y), st);
+      else rc = run_map(b, (OpMultiCaxpy<6, double, float>{m, y}), nsites(y), st);
+    } else {
+      DISPATCH(y.nr, xdbl || y.prec == P64, rc = run_map(b, (OpMultiCaxpy<NR, T, T>{m, y}), nsites(y), st));
+    }
     if (rc) return rc;
   }
   return DIRAC_OK;

@@ -11,10 +11,12 @@
 //
 // FP32/FP16 storage: the block's forward links and clover are copied into shared
 // memory in their storage format (raw chunks: binary16 stays binary16, so an FP16
-// block needs 87 KB and two CTAs fit on an SM) and decoded on use; the residual r
-// lives in shared memory in FP32, x in registers; reductions are warp shuffles plus
-// one shared-memory stage. FP64 storage: r in shared memory, links and clover read
-// through the read-only cache.
+// block needs 87 KB and two CTAs fit on an SM) and decoded on use; the clover's FP16
+// per-site norm scales the 6-component input instead of the 36 entries. The hopping
+// sum is accumulated unscaled and multiplied by -kappa once, only a wrapping t hop
+// with antiperiodic time taking its sign. The residual r lives in shared memory in
+// FP32, x in registers; reductions are warp shuffles plus one shared-memory stage.
+// FP64 storage: r in shared memory, links and clover read through the read-only cache.
 #include "internal.h"
 #include "wilson.cuh"
 
@@ -71,6 +73,65 @@ __device__ __forceinline__ void copy_chunk(char* dst, const char* src) {
   else *reinterpret_cast<int*>(dst) = __ldg(reinterpret_cast<const int*>(src));
 }
 
+// The 36 stored reals of chirality block `blk` of site i, without the FP16 per-site
+// norm, which is returned instead (1 for FP32 / FP64): A_blk = n * v.
+template <int PREC, bool NC, typename T>
+__device__ __forceinline__ T clover_block_raw(const char* b, int stride, int i, int blk, T v[36]) {
+  if constexpr (PREC == P16) {
+    const float n = ld_chunk<float, NC>(b + (size_t)144 * stride + (size_t)i * 4);
+    float f[40];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) unpack_half8(ld_chunk<int4, NC>(b + ((size_t)(4 * blk + k) * stride + i) * 16), f + 8 * k);
+    const int off = 4 * blk;  // block 1 starts 4 halves into chunk 4
+#pragma unroll
+    for (int k = 0; k < 36; ++k) v[k] = f[k + off];
+    return n;
+  } else {
+    clover_block<PREC, NC, T>(b, stride, i, blk, v);
+    return (T)1;
+  }
+}
+
+// The 12 reals of chirality half `blk` (spins 2 blk, 2 blk + 1) of site i of the
+// residual in shared memory.
+template <int RP, typename T>
+__device__ __forceinline__ void r_chirality_half(const char* r_s, int nbs, int i, int blk, T v[12]) {
+  if constexpr (RP == P64) {
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      const double2 q = *reinterpret_cast<const double2*>(r_s + ((size_t)(6 * blk + k) * nbs + i) * 16);
+      v[2 * k] = q.x; v[2 * k + 1] = q.y;
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const float4 q = *reinterpret_cast<const float4*>(r_s + ((size_t)(3 * blk + k) * nbs + i) * 16);
+      v[4 * k] = q.x; v[4 * k + 1] = q.y; v[4 * k + 2] = q.z; v[4 * k + 3] = q.w;
+    }
+  }
+}
+
+// y += A x for one Hermitian 6x6 block (d[6], then 15 complex L_ij, i>j)
+template <typename T>
+__device__ __forceinline__ void herm6_mac(const T* blk, const C<T> x[6], C<T> y[6]) {
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    y[i].r = fma(blk[i], x[i].r, y[i].r);
+    y[i].i = fma(blk[i], x[i].i, y[i].i);
+  }
+  int o = 6;
+#pragma unroll
+  for (int i = 1; i < 6; ++i) {
+#pragma unroll
+    for (int j = 0; j < i; ++j) {
+      C<T> l = {blk[o], blk[o + 1]};
+      o += 2;
+      cmac(y[i], l, x[j]);   // y_i += L_ij x_j
+      cmacc(y[j], l, x[i]);  // y_j += conj(L_ij) x_i
+    }
+  }
+}
+
 template <int PREC, int R>
 __global__ void __launch_bounds__(kMaxBlockSites, (SchwarzLayout<PREC, R>::kMinBlocks))
     schwarz_kernel(const SchwarzArg a) {
@@ -110,9 +171,10 @@ __global__ void __launch_bounds__(kMaxBlockSites, (SchwarzLayout<PREC, R>::kMinB
   const size_t hb = SpinorIO<PREC, 24>::half_bytes(Vh);
   const char* clov_g = a.clover + par * CloverIO<PREC>::parity_bytes(Vh);
 
-  // neighbour local indices and boundary factors, -1 where the hop leaves the block
+  // neighbour local indices, -1 where the hop leaves the block, and the sign of the
+  // two t hops (-1 for a wrapping hop with antiperiodic time)
   int nbr[8];
-  T nbc[8];
+  T tsign[2] = {(T)1, (T)1};
   {
     int stride = 1;
 #pragma unroll
@@ -120,15 +182,13 @@ __global__ void __launch_bounds__(kMaxBlockSites, (SchwarzLayout<PREC, R>::kMinB
 #pragma unroll
       for (int dir = 0; dir < 2; ++dir) {
         int ln = l[mu] + (dir == 0 ? 1 : -1);
-        T bc = (T)(-a.kappa);  // -kappa folded into the hop
         bool ok = true;
         if (ln == a.b[mu] || ln < 0) {
           if (a.b[mu] != g.L[mu]) ok = false;
           ln = dir == 0 ? 0 : a.b[mu] - 1;
-          if (mu == 3 && g.apbc) bc = -bc;
+          if (mu == 3 && g.apbc) tsign[dir] = (T)-1;
         }
         nbr[2 * mu + dir] = ok ? t + (ln - l[mu]) * stride : -1;
-        nbc[2 * mu + dir] = bc;
       }
       stride *= a.b[mu];
     }
@@ -163,28 +223,17 @@ __global__ void __launch_bounds__(kMaxBlockSites, (SchwarzLayout<PREC, R>::kMinB
   }
   __syncthreads();
 
+  const T mk = (T)(-a.kappa);
   for (int step = 0; step < a.steps; ++step) {
     T p[24];
     T red3[3] = {0, 0, 0};
     if (active) {
-      // p = Ahat r - kappa D_B r on this site: the clover part first
+      // p = Ahat r - kappa D_B r on this site: the hopping sum first, unscaled
       C<T> acc[4][3];
-      {
-        T rv[24];
-        SpinorIO<RP, 24>::template load<false>(r_s, nbs, t, rv);
 #pragma unroll
-        for (int blk = 0; blk < 2; ++blk) {
-          T cl[36];
-          if constexpr (L::kStage) clover_block<PREC, false>((const char*)c_s, nbs, t, blk, cl);
-          else clover_block<PREC, true>(clov_g, Vh, cb, blk, cl);
-          C<T> in6[6], out6[6];
+      for (int s = 0; s < 4; ++s)
 #pragma unroll
-          for (int k = 0; k < 6; ++k) in6[k] = C<T>{rv[12 * blk + 2 * k], rv[12 * blk + 2 * k + 1]};
-          herm6_mv<T>(cl, in6, out6);
-#pragma unroll
-          for (int k = 0; k < 6; ++k) acc[2 * blk + k / 3][k % 3] = out6[k];
-        }
-      }
+        for (int c = 0; c < 3; ++c) acc[s][c] = C<T>{0, 0};
 #pragma unroll
       for (int mu = 0; mu < 4; ++mu) {
 #pragma unroll
@@ -208,12 +257,33 @@ __global__ void __launch_bounds__(kMaxBlockSites, (SchwarzLayout<PREC, R>::kMinB
             }
           }
           const T s = dir == 0 ? (T)-1 : (T)1;
-          const T f = nbc[2 * mu + dir];
-          if (mu == 0) wilson_hop<0>(acc, psi, U, dir == 1, s, f);
-          if (mu == 1) wilson_hop<1>(acc, psi, U, dir == 1, s, f);
-          if (mu == 2) wilson_hop<2>(acc, psi, U, dir == 1, s, f);
-          if (mu == 3) wilson_hop<3>(acc, psi, U, dir == 1, s, f);
+          if (mu == 0) wilson_hop<0>(acc, psi, U, dir == 1, s, (T)1);
+          if (mu == 1) wilson_hop<1>(acc, psi, U, dir == 1, s, (T)1);
+          if (mu == 2) wilson_hop<2>(acc, psi, U, dir == 1, s, (T)1);
+          if (mu == 3) wilson_hop<3>(acc, psi, U, dir == 1, s, tsign[dir]);
         }
+      }
+#pragma unroll
+      for (int s = 0; s < 4; ++s)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) acc[s][c] = C<T>{mk * acc[s][c].r, mk * acc[s][c].i};
+      // + Ahat r, chirality block by block; the FP16 norm scales the 6-component input
+#pragma unroll
+      for (int blk = 0; blk < 2; ++blk) {
+        T cl[36], rv[12];
+        T n;
+        if constexpr (L::kStage) n = clover_block_raw<PREC, false, T>((const char*)c_s, nbs, t, blk, cl);
+        else n = clover_block_raw<PREC, true, T>(clov_g, Vh, cb, blk, cl);
+        r_chirality_half<RP>(r_s, nbs, t, blk, rv);
+        C<T> in6[6], out6[6];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+          in6[k] = C<T>{n * rv[2 * k], n * rv[2 * k + 1]};
+          out6[k] = acc[2 * blk + k / 3][k % 3];
+        }
+        herm6_mac<T>(cl, in6, out6);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) acc[2 * blk + k / 3][k % 3] = out6[k];
       }
       T rv[24];
       SpinorIO<RP, 24>::template load<false>(r_s, nbs, t, rv);

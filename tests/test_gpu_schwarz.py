@@ -18,8 +18,10 @@ pytestmark = pytest.mark.gpu
     ((4, 4, 4, 4), (4, 4, 4, 4), 4),     # one block = the lattice: plain MR with wraps
     ((8, 4, 6, 4), (4, 2, 6, 2), 2),     # block spans the z extent
     ((4, 4, 4, 8), (1, 1, 1, 1), 3),     # single-site blocks: MR on the clover matrix
+    ((8, 4, 4, 4), (4, 2, 2, 4), 3),     # block spans the antiperiodic t extent only
 ])
-@pytest.mark.parametrize("prec,recon", [(F64, 18), (F64, 12), (F32, 12), (F16, 12), (F16, 18)])
+@pytest.mark.parametrize("prec,recon", [(F64, 18), (F64, 12), (F32, 12), (F32, 18), (F32, 8),
+                                        (F16, 12), (F16, 18), (F16, 8)])
 def test_schwarz_matches_oracle(dirac, dims, block, steps, prec, recon):
     kappa, csw = 0.124, 1.0
     U = synth.wilson_gauge(dims, 0.5, 2, 500 + sum(dims))
