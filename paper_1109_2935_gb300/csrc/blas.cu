@@ -264,6 +264,146 @@ template <int NR, typename T, bool DOT> struct OpCaxpyNorm {
     }
   }
 };
+// ---- all-FP16 Wilson fields (the FP16 Krylov spaces of the mixed solvers): every input
+// of a site is loaded as its raw binary16 chunks and norm (13 registers instead of 24) and
+// decoded where it is used, so three CTAs fit per SM with all loads of a site in flight.
+struct RawH { int4 q[3]; float n; };
+
+__device__ __forceinline__ RawH raw_h(const FieldRef& f, int s) {
+  const int q = s >= f.Vh ? 1 : 0;
+  const int cb = s - q * f.Vh;
+  const char* b = f.p + q * f.hb;
+  RawH r;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) r.q[k] = *reinterpret_cast<const int4*>(b + ((size_t)k * f.Vh + cb) * 16);
+  r.n = reinterpret_cast<const float*>(b + (size_t)48 * f.Vh)[cb];
+  return r;
+}
+
+// decoded exactly as SpinorIO<P16, 24>::load decodes a site
+__device__ __forceinline__ void dec_h(const RawH& r, float v[24]) {
+#pragma unroll
+  for (int k = 0; k < 3; ++k) unpack_half8(r.q[k], v + 8 * k);
+#pragma unroll
+  for (int k = 0; k < 24; ++k) v[k] *= r.n;
+}
+
+static bool all_h24(std::initializer_list<const FieldRef*> fs) {
+  for (auto f : fs) if (f->prec != P16 || f->nr != 24) return false;
+  return true;
+}
+
+// OpCaxpyNorm on all-FP16 Wilson fields
+template <bool DOT> struct OpCaxpyNormH {
+  static constexpr int kMinBlocks = 3;
+  FieldRef x, y, w; Cf a;
+  __device__ void operator()(int i, double* acc) const {
+    float ar, ai;
+    cf_get(a, ar, ai);
+    const RawH rx = raw_h(x, i), ry = raw_h(y, i);
+    const bool wy = DOT && w.p == y.p;
+    RawH rw = rx;
+    if (DOT && !wy) rw = raw_h(w, i);
+    float v[24];
+    {
+      float u[24];
+      dec_h(rx, u);
+      dec_h(ry, v);
+#pragma unroll
+      for (int k = 0; k < 12; ++k) {
+        const float xr = u[2 * k], xi = u[2 * k + 1];
+        v[2 * k] += ar * xr - ai * xi;
+        v[2 * k + 1] += ar * xi + ai * xr;
+      }
+    }
+    site_store_q<24>(y, i, v);  // reduce what is stored
+    if constexpr (DOT) {
+      float ww[24];
+      if (wy) {
+#pragma unroll
+        for (int k = 0; k < 24; ++k) ww[k] = v[k];
+      } else {
+        dec_h(rw, ww);
+      }
+      acc_norm_dot<24, float>(v, ww, acc);
+    } else {
+      acc_norm_dot<24, float>(v, nullptr, acc);
+    }
+  }
+};
+
+// OpBicgXR with p, s, t, w all-FP16 Wilson fields (xs any non-FP64 precision)
+struct OpBicgXRH {
+  static constexpr int kMinBlocks = 2;
+  FieldRef p, s, t, xs, w; Cf a, b, c;
+  __device__ void operator()(int i, double* acc) const {
+    float ar, ai, br, bi, cr, ci;
+    cf_get(a, ar, ai);
+    cf_get(b, br, bi);
+    cf_get(c, cr, ci);
+    const RawH rp = raw_h(p, i), rs = raw_h(s, i), rt = raw_h(t, i), rw = raw_h(w, i);
+    float ux[24], us[24];
+    site_load<24>(xs, i, ux);
+    dec_h(rs, us);
+    {
+      float up[24];
+      dec_h(rp, up);
+#pragma unroll
+      for (int k = 0; k < 12; ++k) {
+        ux[2 * k] += ar * up[2 * k] - ai * up[2 * k + 1] + br * us[2 * k] - bi * us[2 * k + 1];
+        ux[2 * k + 1] += ar * up[2 * k + 1] + ai * up[2 * k] + br * us[2 * k + 1] + bi * us[2 * k];
+      }
+    }
+    site_store<24>(xs, i, ux);
+    {
+      float ut[24];
+      dec_h(rt, ut);
+#pragma unroll
+      for (int k = 0; k < 12; ++k) {
+        const float tr = ut[2 * k], ti = ut[2 * k + 1];
+        us[2 * k] += cr * tr - ci * ti;
+        us[2 * k + 1] += cr * ti + ci * tr;
+      }
+    }
+    site_store_q<24>(s, i, us);
+    float ww[24];
+    dec_h(rw, ww);
+    acc_norm_dot<24, float>(us, ww, acc);
+  }
+};
+
+// OpScaleCdot on all-FP16 Wilson fields
+struct OpScaleCdotH {
+  static constexpr int kMinBlocks = 3;
+  FieldRef x, y; Cf s;
+  __device__ void operator()(int i, double* acc) const {
+    float sr, si;
+    cf_get(s, sr, si);
+    const bool xy = x.p == y.p;
+    const RawH rx = raw_h(x, i);
+    RawH ry = rx;
+    if (!xy) ry = raw_h(y, i);
+    float u[24], v[24];
+    dec_h(rx, u);
+#pragma unroll
+    for (int k = 0; k < 24; ++k) u[k] *= sr;
+    site_store_q<24>(x, i, u);
+    if (xy) {
+#pragma unroll
+      for (int k = 0; k < 24; ++k) v[k] = u[k];
+    } else {
+      dec_h(ry, v);
+    }
+    float re = 0, im = 0;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      re = fma(u[2 * k], v[2 * k], re); re = fma(u[2 * k + 1], v[2 * k + 1], re);
+      im = fma(u[2 * k], v[2 * k + 1], im); im = fma(-u[2 * k + 1], v[2 * k], im);
+    }
+    acc[0] += (double)re; acc[1] += (double)im;
+  }
+};
+
 // xs += a p + b s ;  s += c t (s becomes r) ; ||r||^2, (w, r)     (BiCGstab; p, s, t
 // and xs are distinct and loaded before the first store, w after the last)
 template <int NR, typename T> struct OpBicgXR {
@@ -514,8 +654,11 @@ static int run_map(Blas* b, const Op& op, int n, cudaStream_t st) {
 template <class Op>
 static int run_reduce(Blas* b, const Op& op, int n, double* out, int nout, cudaStream_t st,
                       double* dres) {
+  // one wave of resident CTAs when the op asks for several per SM, else 4 per SM
+  constexpr int kMaxGrid = MinBlocks<Op>::value > 1 ? 152 * MinBlocks<Op>::value : kRedBlocks;
+  static_assert(kMaxGrid <= kRedBlocks, "partials buffer");
   int grid = (n + kThreads - 1) / kThreads;
-  if (grid > kRedBlocks) grid = kRedBlocks;
+  if (grid > kMaxGrid) grid = kMaxGrid;
   if (grid < 1) grid = 1;
   blas_reduce_kernel<Op><<<grid, kThreads, 0, st>>>(op, n, b->partials, b->ticket, dres ? dres : b->dev_res);
   int rc = check(b, "blas reduce kernel");
@@ -569,16 +712,20 @@ int blas_cdot_norm(Blas* b, const FieldRef& x, const FieldRef& y, double out[3],
 }
 int blas_caxpy_norm(Blas* b, Cf a, const FieldRef& x, const FieldRef& y, double* out, cudaStream_t st,
                     double* dres) {
+  if (all_h24({&x, &y})) return run_reduce(b, (OpCaxpyNormH<false>{x, y, y, a}), nsites(y), out, 1, st, dres);
   DISPATCH(y.nr, any64({&x, &y}),
            return run_reduce(b, (OpCaxpyNorm<NR, T, false>{x, y, y, a}), nsites(y), out, 1, st, dres));
 }
 int blas_caxpy_norm_dot(Blas* b, Cf a, const FieldRef& x, const FieldRef& y, const FieldRef& w,
                         double out[3], cudaStream_t st, double* dres) {
+  if (all_h24({&x, &y, &w})) return run_reduce(b, (OpCaxpyNormH<true>{x, y, w, a}), nsites(y), out, 3, st, dres);
   DISPATCH(y.nr, any64({&x, &y, &w}),
            return run_reduce(b, (OpCaxpyNorm<NR, T, true>{x, y, w, a}), nsites(y), out, 3, st, dres));
 }
 int blas_bicg_xr(Blas* b, Cf a, const FieldRef& p, Cf bb, const FieldRef& s, Cf c, const FieldRef& t,
                  const FieldRef& xs, const FieldRef& w, double out[3], cudaStream_t st, double* dres) {
+  if (all_h24({&p, &s, &t, &w}) && xs.prec != P64 && xs.nr == 24)
+    return run_reduce(b, (OpBicgXRH{p, s, t, xs, w, a, bb, c}), nsites(s), out, 3, st, dres);
   DISPATCH(s.nr, any64({&p, &s, &t, &xs, &w}),
            return run_reduce(b, (OpBicgXR<NR, T>{p, s, t, xs, w, a, bb, c}), nsites(s), out, 3, st, dres));
 }
@@ -589,6 +736,7 @@ int blas_cg_update(Blas* b, Cf a, const FieldRef& p, Cf c, const FieldRef& Ap, c
 }
 int blas_scale_cdot(Blas* b, Cf s, const FieldRef& x, const FieldRef& y, double out[2], cudaStream_t st,
                     double* dres) {
+  if (all_h24({&x, &y})) return run_reduce(b, (OpScaleCdotH{x, y, s}), nsites(x), out, 2, st, dres);
   DISPATCH(x.nr, any64({&x, &y}),
            return run_reduce(b, (OpScaleCdot<NR, T>{x, y, s}), nsites(x), out, 2, st, dres));
 }
