@@ -404,6 +404,53 @@ struct OpScaleCdotH {
   }
 };
 
+// OpCdotNorm on all-FP16 Wilson fields: (x, y) and ||x||^2
+struct OpCdotNormH {
+  static constexpr int kMinBlocks = 3;
+  FieldRef x, y;
+  __device__ void operator()(int i, double* acc) const {
+    const RawH rx = raw_h(x, i), ry = raw_h(y, i);
+    float u[24], v[24];
+    dec_h(rx, u);
+    dec_h(ry, v);
+    float re = 0, im = 0, nn = 0;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      const float xr = u[2 * k], xi = u[2 * k + 1], yr = v[2 * k], yi = v[2 * k + 1];
+      re = fma(xr, yr, re); re = fma(xi, yi, re);
+      im = fma(xr, yi, im); im = fma(-xi, yr, im);
+      nn = fma(xr, xr, nn); nn = fma(xi, xi, nn);
+    }
+    acc[0] += (double)re; acc[1] += (double)im; acc[2] += (double)nn;
+  }
+};
+
+// OpPUpdate on all-FP16 Wilson fields: p = r + b p + c v
+struct OpPUpdateH {
+  static constexpr int kMinBlocks = 3;
+  FieldRef r, v, p; Cf b, c;
+  __device__ void operator()(int i, double*) const {
+    float br, bi, cr, ci;
+    cf_get(b, br, bi);
+    cf_get(c, cr, ci);
+    const RawH rr = raw_h(r, i), rv = raw_h(v, i), rp = raw_h(p, i);
+    float ur[24], up[24];
+    dec_h(rp, up);
+    dec_h(rr, ur);
+    {
+      float uv[24];
+      dec_h(rv, uv);
+#pragma unroll
+      for (int k = 0; k < 12; ++k) {
+        const float pr = up[2 * k], pi = up[2 * k + 1], vr = uv[2 * k], vi = uv[2 * k + 1];
+        up[2 * k] = ur[2 * k] + br * pr - bi * pi + cr * vr - ci * vi;
+        up[2 * k + 1] = ur[2 * k + 1] + br * pi + bi * pr + cr * vi + ci * vr;
+      }
+    }
+    site_store<24>(p, i, up);
+  }
+};
+
 // xs += a p + b s ;  s += c t (s becomes r) ; ||r||^2, (w, r)     (BiCGstab; p, s, t
 // and xs are distinct and loaded before the first store, w after the last)
 template <int NR, typename T> struct OpBicgXR {
@@ -568,7 +615,7 @@ template <class Op> struct MinBlocks<Op, std::void_t<decltype(Op::kMinBlocks)>> 
 };
 
 template <class Op>
-__global__ void __launch_bounds__(kThreads) blas_map_kernel(Op op, int n) {
+__global__ void __launch_bounds__(kThreads, MinBlocks<Op>::value) blas_map_kernel(Op op, int n) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) op(i, nullptr);
 }
 
@@ -644,8 +691,9 @@ static int check(Blas* b, const char* what) {
 
 template <class Op>
 static int run_map(Blas* b, const Op& op, int n, cudaStream_t st) {
+  constexpr int kMaxGrid = MinBlocks<Op>::value > 1 ? 152 * MinBlocks<Op>::value : 152 * 16;
   int grid = (n + kThreads - 1) / kThreads;
-  if (grid > 152 * 16) grid = 152 * 16;
+  if (grid > kMaxGrid) grid = kMaxGrid;
   if (grid < 1) grid = 1;
   blas_map_kernel<Op><<<grid, kThreads, 0, st>>>(op, n);
   return check(b, "blas map kernel");
@@ -696,17 +744,20 @@ int blas_axpby(Blas* b, Cf a, const FieldRef& x, Cf bb, const FieldRef& y, cudaS
 }
 int blas_pupdate(Blas* b, const FieldRef& r, Cf beta, Cf c, const FieldRef& v, const FieldRef& p,
                  cudaStream_t st) {
+  if (all_h24({&r, &v, &p})) return run_map(b, (OpPUpdateH{r, v, p, beta, c}), nsites(p), st);
   DISPATCH(p.nr, any64({&r, &v, &p}), return run_map(b, (OpPUpdate<NR, T>{r, v, p, beta, c}), nsites(p), st));
 }
 int blas_norm2(Blas* b, const FieldRef& x, double* out, cudaStream_t st, double* dres) {
   DISPATCH(x.nr, any64({&x}), return run_reduce(b, (OpNorm2<NR, T>{x}), nsites(x), out, 1, st, dres));
 }
 int blas_cdot(Blas* b, const FieldRef& x, const FieldRef& y, double out[2], cudaStream_t st, double* dres) {
+  if (all_h24({&x, &y})) return run_reduce(b, (OpCdotNormH{x, y}), nsites(x), out, 2, st, dres);
   DISPATCH(x.nr, any64({&x, &y}),
            return run_reduce(b, (OpCdotNorm<NR, T>{x, y}), nsites(x), out, 2, st, dres));
 }
 int blas_cdot_norm(Blas* b, const FieldRef& x, const FieldRef& y, double out[3], cudaStream_t st,
                    double* dres) {
+  if (all_h24({&x, &y})) return run_reduce(b, (OpCdotNormH{x, y}), nsites(x), out, 3, st, dres);
   DISPATCH(x.nr, any64({&x, &y}),
            return run_reduce(b, (OpCdotNorm<NR, T>{x, y}), nsites(x), out, 3, st, dres));
 }
