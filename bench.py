@@ -221,6 +221,10 @@ def main():
     ap.add_argument("--dims", type=int, nargs=4, default=list(DIMS),
                     help="lattice extents (profiling cases use a smaller lattice)")
     ap.add_argument("--precs", default="f64,f32,f16", help="precisions to keep and time")
+    ap.add_argument("--solve-profile", choices=["gcr_dd", "bicgstab", "bicgstab_eo"],
+                    help="run only this mixed solve (FP16 Krylov space and preconditioner) at kappa 0.124 on "
+                         "--dims, for a launch list; prints its statistics as one JSON line")
+    ap.add_argument("--solve-iters", type=int, default=48, help="iteration budget of --solve-profile")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -233,6 +237,8 @@ def main():
     dev = torch.device("cuda", local)
     from paper_1109_2935_gb300 import dirac, synth
 
+    if args.solve_profile:
+        return solve_profile(args, dirac, synth, dev)
     dims = tuple(args.dims)
     precs = [p for p in args.precs.split(",") if p in PREC_ID]
     if HEADLINE not in precs:
@@ -793,6 +799,27 @@ def measure_ptc(dirac, synth, dev, stream):
     net.close()
     lat.close()
     return out
+
+
+def solve_profile(args, dirac, synth, dev):
+    """One mixed solve of the bench workload with a bounded iteration budget, so that a
+    launch list covers whole solver steps (restarts and reliable updates included)."""
+    import torch
+    dims = tuple(args.dims)
+    alg = {"gcr_dd": dirac.GCR_DD, "bicgstab": dirac.BICGSTAB, "bicgstab_eo": dirac.BICGSTAB_EO}[args.solve_profile]
+    lat = dirac.Lattice(dims, dirac.WILSON_CLOVER, kappa=KAPPA_SOLVE, csw=CSW, block=BLOCK,
+                        mr_steps=MR_STEPS, recon=(18, 12, 12))
+    lat.load_gauge(synth.wilson_gauge(dims, SIGMA, SMEAR, SEED_GAUGE, device=dev))
+    b = lat.to_device(synth.wilson_spinor(dims, SEED_SRC, device=dev), dirac.F64)
+    x = lat.new_field(dirac.F64)
+    torch.cuda.synchronize()
+    st = lat.solve(x, b, alg, tol=1e-10, max_iter=args.solve_iters, k_max=16, delta=0.1,
+                   prec_sloppy=dirac.F16, prec_precond=dirac.F16, raise_on_error=False)
+    torch.cuda.synchronize()
+    print(json.dumps({"solve_profile": args.solve_profile, "dims": list(dims), "kappa": KAPPA_SOLVE,
+                      "stats": {k: (float(f"{v:.4g}") if isinstance(v, float) else v) for k, v in st.items()}}))
+    lat.close()
+    return 0
 
 
 def run_solves(dirac, synth, U, src, dev):
