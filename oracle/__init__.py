@@ -14,10 +14,15 @@ gamma     Euclidean gamma matrices in a chiral basis (Sec. 5, "similarity transf
 wilson    Wilson dslash, clover field, Wilson-clover operator (Eq. 2)
 staggered improved staggered (asqtad) dslash and operator (Eq. 3)
 codecs    gauge 12/8-real compression and 16-bit storage (Sec. 5, strategies (a) and (c))
-solvers   MR / additive Schwarz (Sec. 3.2, 8.1), CG, BiCGstab (Sec. 3.1), GCR-DD (Algorithm 1)
+solvers   MR / additive Schwarz (Sec. 3.2, 8.1), CG, BiCGstab (Sec. 3.1), GCR-DD (Algorithm 1),
+          multi-shift CG (Eq. 4)
+ptc       gauge-equivariant parallel-transport network used as a learned preconditioner K of
+          the flexible GCR (not in the paper; Algorithm 1 admits any K): forward, adjoint,
+          loss and weight gradients, Adam
 
 Pins: every function here is checked by ``tests/test_oracle_*.py`` against closed
 forms (free-field plane waves, constant abelian field strength), symmetries
-(gamma5-hermiticity, anti-hermiticity, gauge covariance) and brute-force dense
-linear algebra on tiny lattices.
+(gamma5-hermiticity, anti-hermiticity, gauge covariance), brute-force dense
+linear algebra on tiny lattices, rounding bounds of the storage formats, values
+counted by hand (boundary crossings) and finite differences (network gradients).
 """
