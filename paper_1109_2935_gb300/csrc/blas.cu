@@ -302,7 +302,7 @@ template <bool DOT> struct OpCaxpyNormH {
     cf_get(a, ar, ai);
     const RawH rx = raw_h(x, i), ry = raw_h(y, i);
     const bool wy = DOT && w.p == y.p;
-    RawH rw = rx;
+    RawH rw = rx;  // unused when w is y itself
     if (DOT && !wy) rw = raw_h(w, i);
     float v[24];
     {
@@ -381,7 +381,7 @@ struct OpScaleCdotH {
     cf_get(s, sr, si);
     const bool xy = x.p == y.p;
     const RawH rx = raw_h(x, i);
-    RawH ry = rx;
+    RawH ry = rx;  // unused when y is x itself
     if (!xy) ry = raw_h(y, i);
     float u[24], v[24];
     dec_h(rx, u);
