@@ -1,8 +1,11 @@
-"""The t-slab domain decomposition across processes, on CPU: two gloo ranks exchange
+"""The t-slab domain decomposition across processes, on CPU: gloo ranks exchange
 spin-projected faces (paper_1109_2935_gb300/halo.py) and each computes the oracle's
 Wilson-clover operator on its slab plus ghosts, which must equal the whole-lattice
 oracle there; the allreduce of local norms gives the global norm; a rank that never
-sends makes the other's exchange end with ERR_TIMEOUT instead of hanging."""
+sends makes the other's exchange end with ERR_TIMEOUT instead of hanging. With four
+ranks the previous and the next neighbour of a rank are different processes, so a face
+sent the wrong way round would fail the comparison (with two they coincide)."""
+import pytest
 import os
 import socket
 
@@ -84,8 +87,9 @@ def _worker(rank, world, port, q, done):
     q.put((rank, err, n2, n2_ref, timed_out, code))
 
 
-def test_two_rank_halo_exchange_matches_whole_lattice_and_times_out():
-    world, port = 2, _free_port()
+@pytest.mark.parametrize("world", [2, 4])
+def test_rank_halo_exchange_matches_whole_lattice_and_times_out(world):
+    port = _free_port()
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     done = ctx.Event()
@@ -100,4 +104,4 @@ def test_two_rank_halo_exchange_matches_whole_lattice_and_times_out():
         assert err < 1e-13, (rank, err)
         assert abs(n2 - n2_ref) < 1e-12 * n2_ref
     assert got[0][4] and got[0][5] == -8
-    assert not got[1][4]
+    assert not any(g[4] for g in got[1:])
