@@ -1,4 +1,4 @@
-"""The bench's multi-rank path on CPU: two gloo ranks (replicas, no data-path
+"""The bench's multi-rank path on CPU: two or four gloo ranks (replicas, no data-path
 collective) agree on the max time and the summed work, as bench.py reports them."""
 import os
 import socket
@@ -30,8 +30,9 @@ def _worker(rank, world, port, q):
     dist.destroy_process_group()
 
 
-def test_two_rank_max_and_sum():
-    world, port = 2, _free_port()
+@pytest.mark.parametrize("world", [2, 4])
+def test_rank_max_and_sum(world):
+    port = _free_port()
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     procs = [ctx.Process(target=_worker, args=(r, world, port, q)) for r in range(world)]
@@ -41,5 +42,5 @@ def test_two_rank_max_and_sum():
         p.join(120)
         assert p.exitcode == 0
     got = sorted(q.get(timeout=10) for _ in range(world))
-    assert [g[1] for g in got] == [2.0, 2.0]     # max over ranks
-    assert [g[2] for g in got] == [30.0, 30.0]   # work summed over ranks
+    assert [g[1] for g in got] == [float(world)] * world                       # max over ranks
+    assert [g[2] for g in got] == [5.0 * world * (world + 1)] * world          # work summed over ranks
