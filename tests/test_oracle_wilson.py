@@ -206,3 +206,71 @@ def test_schur_complement_equals_dense_block_schur():
     xfull[E] = xe
     x = wilson.schur_reconstruct(U, A, kappa, b, xfull.reshape(shape))
     assert np.linalg.norm(M(x) - b) / np.linalg.norm(b) < 1e-13
+
+
+def _sample_sites(dims, n, seed):
+    """A site sample that always contains both t edges (where antiperiodic hops wrap),
+    a repeated site and an unsorted order."""
+    r = np.random.default_rng(seed)
+    c = all_coords(dims)
+    idx = r.choice(len(c), size=min(n, len(c)), replace=False)
+    edge = np.where((c[:, 3] == 0) | (c[:, 3] == dims[3] - 1))[0][:3]
+    idx = np.concatenate([idx, edge, idx[:1]])
+    return idx, c[idx]
+
+
+@pytest.mark.parametrize("dims,apbc", [((4, 4, 4, 6), True), ((2, 2, 2, 2), True),
+                                       ((2, 4, 2, 4), False)])
+def test_site_subset_clover_matches_whole_lattice(dims, apbc):
+    """clover(U, csw, sites) is the whole-lattice clover field read at those sites."""
+    U, A = _random_fields(dims, seed=21, csw=1.3)
+    idx, xs = _sample_sites(dims, 40, 3)
+    sub = wilson.clover(U, 1.3, xs)
+    whole = A.reshape(-1, 12, 12)[idx]
+    assert np.max(np.abs(sub - whole)) <= 1e-13 * np.max(np.abs(whole))
+
+
+def _codec_half(Ahat):
+    from oracle import codecs
+    return codecs.clover_half(Ahat)
+
+
+def _codec_single(Ahat):
+    from oracle import codecs
+    return codecs.clover_single(Ahat)
+
+
+@pytest.mark.parametrize("dims,apbc", [((4, 4, 4, 6), True), ((2, 2, 2, 2), True),
+                                       ((2, 4, 2, 4), False)])
+@pytest.mark.parametrize("dagger", [False, True])
+@pytest.mark.parametrize("codec", [None, _codec_half, _codec_single])
+def test_apply_M_sites_matches_whole_lattice(dims, apbc, dagger, codec):
+    """apply_M_sites (the checker of every sampled full-size GPU result) equals the
+    whole-lattice M_kappa of Eq. 2 at the sampled sites. With a storage codec the
+    whole-lattice operator is given the clover A' = (codec(1 + 2 kappa A) - 1) / (2 kappa),
+    so that its own 1 + 2 kappa A' is the stored Ahat."""
+    kappa, csw = 0.127, 1.3
+    U, A = _random_fields(dims, seed=22, csw=csw)
+    psi = synth.wilson_spinor(dims, 23).numpy()
+    idx, xs = _sample_sites(dims, 50, 4)
+    got = wilson.apply_M_sites(U, csw, kappa, psi, xs, apbc, dagger, Ahat_codec=codec)
+    if codec is None:
+        Aw = A
+    else:
+        Aw = (codec(np.eye(12) + 2.0 * kappa * A) - np.eye(12)) / (2.0 * kappa)
+    whole = wilson.apply_M(U, Aw, kappa, psi, apbc, dagger=dagger).reshape(-1, 4, 3)[idx]
+    err = np.max(np.abs(got - whole)) / np.max(np.abs(whole))
+    assert err <= 1e-13, err
+    # a dropped clover or hopping term would be far outside this bound
+    assert np.max(np.abs(whole - psi.reshape(-1, 4, 3)[idx])) > 1e-2
+
+
+def test_apply_M_sites_without_clover_is_wilson():
+    """csw = 0: apply_M_sites is the plain Wilson operator 1 - kappa D."""
+    dims = (4, 4, 2, 4)
+    U, _ = _random_fields(dims, seed=24)
+    psi = synth.wilson_spinor(dims, 25).numpy()
+    idx, xs = _sample_sites(dims, 20, 5)
+    got = wilson.apply_M_sites(U, 0.0, 0.11, psi, xs, True, False)
+    whole = wilson.apply_M(U, None, 0.11, psi, True).reshape(-1, 4, 3)[idx]
+    assert np.max(np.abs(got - whole)) <= 1e-13 * np.max(np.abs(whole))
