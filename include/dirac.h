@@ -193,10 +193,14 @@ int dirac_convert(dirac_ctx* ctx, void* dst, dirac_prec dprec, const void* src, 
  * the library holds it until the process exits). One call covers at most 8,388,608
  * sites (npar * sites_per_parity); larger fields are rejected with DIRAC_ERR_ARG and
  * a message in `err` (err may be NULL; err_len bytes including the terminator).
+ * x, y and result must be device (or managed) memory; a host pointer is rejected with
+ * DIRAC_ERR_ARG before anything is queued. An error already pending from earlier
+ * asynchronous work is reported (DIRAC_ERR_CUDA, left pending) and nothing is queued.
  * Every call shares the array: calls that overlap on the GPU (other streams or other
  * host threads) race and give wrong results; serialise them. The first call on each
- * device looks up the array's device address (once per device, with that device
- * current); make that first call before any stream capture. */
+ * device looks up the array's device address (once per device and CUDA context, with
+ * that device current; again after a device reset); make that first call before any
+ * stream capture. */
 int dirac_cdot_noalloc(const void* x, const void* y, dirac_prec prec, int reals_per_site,
                        long long sites_per_parity, dirac_parity parity, double* result,
                        void* stream, char* err, size_t err_len);

@@ -852,7 +852,48 @@ static constexpr long long kNoAllocMaxSites =
 static __device__ __align__(256) unsigned long long g_noalloc_scratch[3 * kNoAllocMaxBlocks + 1];
 
 static std::mutex g_noalloc_mu;
-static void* g_noalloc_addr[128] = {};  // device address of the array, per device
+// Device address of the array per device, and the id of the CUDA context it was looked
+// up in: a device reset (or another context on the same device) loads the module again,
+// possibly at another address, so the address is looked up again when the id changes.
+static void* g_noalloc_addr[128] = {};
+static unsigned long long g_noalloc_ctx[128] = {};
+
+// Id of the current CUDA context (0 if none is current or the driver lacks the call),
+// through the runtime's driver entry points so that the library needs no -lcuda.
+static unsigned long long noalloc_ctx_id() {
+  typedef int (*get_current_t)(void**);
+  typedef int (*get_id_t)(void*, unsigned long long*);
+  static get_current_t get_current = nullptr;
+  static get_id_t get_id = nullptr;
+  static bool looked_up = false;
+  if (!looked_up) {
+    looked_up = true;
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_current = (get_current_t)f;
+    f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_id = (get_id_t)f;
+    cudaGetLastError();
+  }
+  void* ctx = nullptr;
+  unsigned long long id = 0;
+  if (!get_current || !get_id || get_current(&ctx) != 0 || !ctx || get_id(ctx, &id) != 0) return 0;
+  return id;
+}
+
+// true when the GPU can address p as device memory (device or managed allocation)
+static bool noalloc_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();  // the query's own error, nothing was pending before it
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
 
 static int noalloc_fail(char* err, size_t len, int code, const std::string& msg) {
   if (err && len) {
@@ -884,21 +925,38 @@ extern "C" int dirac_cdot_noalloc(const void* x, const void* y, dirac_prec prec,
     return noalloc_fail(err, err_len, DIRAC_ERR_ARG,
                         "dirac_cdot_noalloc: " + std::to_string(n) + " sites exceed the maximum of " +
                             std::to_string(kNoAllocMaxSites) + " for its fixed scratch array");
+  // an error left by earlier asynchronous work is reported, not taken over: peek (the
+  // caller can still read it) and queue nothing
+  cudaError_t pending = cudaPeekAtLastError();
+  if (pending != cudaSuccess)
+    return noalloc_fail(err, err_len, DIRAC_ERR_CUDA,
+                        std::string("dirac_cdot_noalloc: an earlier CUDA error is pending (") +
+                            cudaGetErrorString(pending) + "); nothing was queued");
+  // the kernel dereferences all three pointers: a host pointer would fault the GPU
+  if (!noalloc_device_ptr(x) || !noalloc_device_ptr(y))
+    return noalloc_fail(err, err_len, DIRAC_ERR_ARG, "dirac_cdot_noalloc: x and y must be device memory");
+  if (!noalloc_device_ptr(result))
+    return noalloc_fail(err, err_len, DIRAC_ERR_ARG,
+                        "dirac_cdot_noalloc: result must be device memory (3 doubles)");
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 128)
     return noalloc_fail(err, err_len, DIRAC_ERR_CUDA, "dirac_cdot_noalloc: cudaGetDevice failed");
   void* base = nullptr;
   {
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_addr[dev]) {
-      // once per device, with that device current: the host-side name of the array is
-      // not a device address, so ask the runtime for the real one
-      cudaError_t e = cudaGetSymbolAddress(&g_noalloc_addr[dev], g_noalloc_scratch);
+    const unsigned long long ctx = noalloc_ctx_id();
+    if (!g_noalloc_addr[dev] || ctx == 0 || ctx != g_noalloc_ctx[dev]) {
+      // set-up, with the device current: the host-side name of the array is not a
+      // device address, so ask the runtime for the real one (again after a reset)
+      void* a = nullptr;
+      cudaError_t e = cudaGetSymbolAddress(&a, g_noalloc_scratch);
       if (e != cudaSuccess) {
         g_noalloc_addr[dev] = nullptr;
         return noalloc_fail(err, err_len, DIRAC_ERR_CUDA,
                             std::string("dirac_cdot_noalloc: cudaGetSymbolAddress: ") + cudaGetErrorString(e));
       }
+      g_noalloc_addr[dev] = a;
+      g_noalloc_ctx[dev] = noalloc_ctx_id();
     }
     base = g_noalloc_addr[dev];
   }

@@ -162,3 +162,60 @@ def test_asqtad_48x144(dirac):
             check(_at(got, s), ref, prec, 6, f"48^3x144 asqtad D_{parity} prec={prec}")
             del src, out
     lat.close()
+
+
+def _staggered_sampled_residual(fat_n, lng_n, mass, shift, b, x, dims, n=256, seed=11):
+    """||b - ((M^dagger M)_ee + shift) x|| / ||b|| over a random sample of even sites
+    (plus the origin), the oracle evaluating (M^dagger M)_ee = m^2 - 1/4 D_eo D_oe
+    (Sec. 3.1, Eq. 3) one site at a time: D x at the odd sites the sample's hops reach
+    (1- and 3-hops in every direction), then D of that at the sample."""
+    s = _sample(dims, n, parity=0, seed=seed)
+    neigh = []
+    for mu in range(4):
+        for h in (1, -1, 3, -3):
+            y = s.copy()
+            y[:, mu] = (y[:, mu] + h) % dims[mu]
+            neigh.append(y)
+    neigh = np.unique(np.concatenate(neigh), axis=0)
+    x_e = x * staggered.parity_mask(dims, 0)[..., None]
+    dx = staggered.dslash(fat_n, lng_n, x_e, True, neigh)
+    Y = np.zeros_like(x)
+    Y[neigh[:, 3], neigh[:, 2], neigh[:, 1], neigh[:, 0]] = dx
+    ddx = staggered.dslash(fat_n, lng_n, Y, True, s)
+    ax = (mass * mass + shift) * _at(x, s) - 0.25 * ddx
+    bs = _at(b, s)
+    return np.linalg.norm(bs - ax) / np.linalg.norm(bs)
+
+
+def test_asqtad_solves_48x144_oracle_gated(dirac):
+    """The asqtad solves of the benchmark at 48^3x144, m = 0.01: mixed FP64/FP32 CG on
+    (M^dagger M)_ee and the 4-shift multi-shift solve (Eq. 4, Sec. 8.2). The library's
+    FP64 true residual <= 1e-10 for every system, and the oracle's sampled residual
+    agrees (<= 1e-9)."""
+    dims, mass = (48, 48, 48, 144), 0.01
+    fat, lng = synth.asqtad_links(dims, 3001, 3002, device="cuda")
+    src = synth.staggered_spinor(dims, 3003, device="cuda", parity=0)
+    lat = dirac.Lattice(dims, dirac.ASQTAD, mass=mass, recon=(18, 12, 12))
+    lat.load_gauge(fat, 1)
+    lat.load_gauge(lng, 2)
+    fat_n, lng_n = fat.cpu().numpy(), lng.cpu().numpy()
+    del fat, lng
+    torch.cuda.empty_cache()
+    b_n = src.cpu().numpy()
+    b = lat.to_device(src, F64, 0)
+    x = lat.new_field(F64, 0)
+    st = lat.solve(x, b, dirac.CG_EVEN_NORMAL, tol=1e-10, max_iter=6000, delta=0.1, prec_sloppy=F32)
+    assert st["true_rel_resid"] <= 1e-10
+    xn = lat.to_natural(x, F64, 0, device="cpu").numpy()
+    est = _staggered_sampled_residual(fat_n, lng_n, mass, 0.0, b_n, xn, dims)
+    assert est < 1e-9, est
+    shifts = [0.0, 0.0005, 0.005, 0.05]
+    xs = [lat.new_field(F64, 0) for _ in shifts]
+    r = lat.solve_multishift(xs, b, shifts, dirac.CG_EVEN_NORMAL, tol=1e-10, max_iter=6000,
+                             delta=0.1, prec_sloppy=F32)
+    for j, (sg, xj) in enumerate(zip(shifts, xs)):
+        assert r["refine"][j]["true_rel_resid"] <= 1e-10, (j, r["refine"][j])
+        xjn = lat.to_natural(xj, F64, 0, device="cpu").numpy()
+        est = _staggered_sampled_residual(fat_n, lng_n, mass, sg, b_n, xjn, dims, seed=20 + j)
+        assert est < 1e-9, (j, est)
+    lat.close()
