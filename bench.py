@@ -340,6 +340,7 @@ def main():
     ap.add_argument("--no-asqtad", action="store_true", help="skip the asqtad rows")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched multi-RHS row")
     ap.add_argument("--no-ptc", action="store_true", help="skip the learned-preconditioner row")
+    ap.add_argument("--no-wilson-solve", action="store_true", help="skip the 24^3x128 solves")
     ap.add_argument("--asqtad-dims", type=int, nargs=4, default=[48, 48, 48, 144],
                     help="asqtad lattice (48^3x144 unless profiling a smaller case)")
     ap.add_argument("--dims", type=int, nargs=4, default=list(DIMS),
@@ -435,7 +436,7 @@ def main():
 
     # solves (second half of the metric), timed separately
     solves = None
-    if not args.no_solve and dims == DIMS:
+    if not args.no_solve and not args.no_wilson_solve and dims == DIMS:
         solves = run_solves(dirac, synth, U, src, dev)
 
     cpu = None
@@ -469,6 +470,8 @@ def main():
     torch.cuda.empty_cache()
     if not args.no_batch:
         rows["batched_multi_rhs"] = measure_batch(dirac, synth, dev, stream, peak)
+        if not args.no_solve:
+            rows["batched_solves"] = measure_batched_solves(dirac, synth, dev)
     if not args.no_ptc and not args.no_solve:
         rows["ptc_preconditioner"] = measure_ptc(dirac, synth, dev, stream)
     if not args.no_asqtad:
@@ -562,6 +565,10 @@ def measure_wilson_rows(lat, dirac, fields, precs, stream, peak):
     return out
 
 
+# links exp(i sigma H) with sigma = 0.5 and no smoothing: the smoothed field of the
+# 24^3x128 workload is past its critical point at these kappa (no solver converges there),
+# this rougher field is not
+BATCH_SMEAR = 0
 BATCH_LATTICES = (((16, 16, 16, 32), 0.130, 4001), ((24, 24, 24, 64), 0.133, 4003),
                   ((32, 32, 32, 64), 0.136, 4005))
 BATCH_RHS = 12
@@ -585,7 +592,7 @@ def measure_batch_prec(dirac, synth, dev, stream, peak, prec):
     per_rhs = 104 if prec == dirac.F16 else 192
     lats, ins, outs = [], [], []
     for dims, kappa, seed in BATCH_LATTICES:
-        U = synth.wilson_gauge(dims, 0.5, 3, seed, device=dev)
+        U = synth.wilson_gauge(dims, 0.5, BATCH_SMEAR, seed, device=dev)
         lat = dirac.Lattice(dims, dirac.WILSON_CLOVER, kappa=kappa, csw=CSW, recon=(18, 12, 12),
                             prec_mask=(1 << dirac.F64) | (1 << prec))
         lat.load_gauge(U)
@@ -625,6 +632,21 @@ def measure_batch_prec(dirac, synth, dev, stream, peak, prec):
                                  "alg_GBps": round(alg_bytes / (ms / 1e3) / 1e9, 1),
                                  "frac_of_hbm": round(alg_bytes / (ms / 1e3) / 1e9 / peak, 4),
                                  "single_rhs_equiv_GBps": round(single_bytes / (ms / 1e3) / 1e9, 1)}
+    # both kernels of the plan, each timed on its own: the CUDA-core kernel (one warp per
+    # right-hand side) and, with FP16 storage, the tensor-core kernel
+    kinfo = b.kernel_info()
+    res["persistent_batched"]["tensor_cores"] = kinfo["tensor_cores"]
+    kern = {}
+    for kname, on in (("cuda_cores", False), ("tensor_cores", True)):
+        if on and kinfo["tensor_core_ms"] < 0:
+            continue
+        b.set_tensor_cores(on)
+        kms = _event_time(b.apply, 20, stream)
+        kern[kname] = {"ms": round(kms, 4), "alg_GBps": round(alg_bytes / (kms / 1e3) / 1e9, 1),
+                       "frac_of_hbm": round(alg_bytes / (kms / 1e3) / 1e9 / peak, 4),
+                       "site_rhs_per_s": round(sites * BATCH_RHS / (kms / 1e3) / 1e9, 3)}
+    b.set_tensor_cores(kinfo["tensor_cores"])
+    res["kernels"] = kern
     napply = 10
     b.capture(napply, stream)
     ms = _event_time(b.apply, 5, stream) / napply
@@ -635,6 +657,64 @@ def measure_batch_prec(dirac, synth, dev, stream, peak, prec):
     for lat in lats:
         lat.close()
     return res
+
+
+def measure_batched_solves(dirac, synth, dev):
+    """The batched workload's 36 systems (12 right-hand sides on each lattice) solved to a
+    true residual of 1e-10: all together by solve_batched (mixed FP16/FP64 BiCGstab, one
+    iteration of every system at a time on the batched operator) vs the same mixed solver
+    one system at a time vs plain FP64 BiCGstab one system at a time."""
+    import torch
+    lats, xs, bs = [], [], []
+    for dims, kappa, seed in BATCH_LATTICES:
+        U = synth.wilson_gauge(dims, 0.5, BATCH_SMEAR, seed, device=dev)
+        lat = dirac.Lattice(dims, dirac.WILSON_CLOVER, kappa=kappa, csw=CSW, recon=(18, 12, 12),
+                            prec_mask=(1 << dirac.F64) | (1 << dirac.F16))
+        lat.load_gauge(U)
+        fb = lat.field_bytes(dirac.F64)
+        b = torch.empty(BATCH_RHS * fb, dtype=torch.uint8, device=dev)
+        for r in range(BATCH_RHS):
+            lat.import_spinor(b[r * fb:(r + 1) * fb], dirac.F64, -1,
+                              synth.wilson_spinor(dims, seed + 100 + r, device=dev))
+        lats.append(lat)
+        bs.append(b)
+        xs.append(torch.zeros_like(b))
+    torch.cuda.synchronize()
+    nrhs = [BATCH_RHS] * len(lats)
+    out = {"systems": sum(nrhs), "tol": 1e-10, "gauge": "sigma 0.5, no smoothing"}
+    t0 = time.perf_counter()
+    r = dirac.solve_many(lats, xs, bs, nrhs, tol=1e-10, max_iter=4000, delta=0.1, prec_sloppy=dirac.F16,
+                         raise_on_error=False)
+    torch.cuda.synchronize()
+    t_b = time.perf_counter() - t0
+    its = [st["iters"] for st in r["rhs"]]
+    out["batched_mixed_f16"] = {"status": r["status"], "seconds": round(t_b, 3), "iters_max": max(its),
+                                "iters_mean": round(sum(its) / len(its), 1),
+                                "worst_true_rel_resid": float("%.3g" % max(st["true_rel_resid"] for st in r["rhs"]))}
+    for tag, sp, delta in (("sequential_mixed_f16", dirac.F16, 0.1), ("sequential_plain_f64", dirac.F64, 0.0)):
+        tot, itot, worst, status = 0.0, 0, 0.0, "OK"
+        for lat, b in zip(lats, bs):
+            fb = lat.field_bytes(dirac.F64)
+            x = lat.new_field(dirac.F64)
+            for k in range(BATCH_RHS):
+                torch.cuda.synchronize()
+                t1 = time.perf_counter()
+                st = lat.solve(x, b[k * fb:(k + 1) * fb], dirac.BICGSTAB, tol=1e-10, max_iter=4000, delta=delta,
+                               prec_sloppy=sp, raise_on_error=False)
+                torch.cuda.synchronize()
+                tot += time.perf_counter() - t1
+                itot += st["iters"]
+                worst = max(worst, st["true_rel_resid"])
+                if st["status"] != "OK":
+                    status = st["status"]
+        out[tag] = {"status": status, "seconds": round(tot, 3), "iters_total": itot,
+                    "worst_true_rel_resid": float("%.3g" % worst)}
+    b_s = out["batched_mixed_f16"]["seconds"]
+    out["speedup_vs_sequential_mixed"] = round(out["sequential_mixed_f16"]["seconds"] / b_s, 3)
+    out["speedup_vs_plain_f64"] = round(out["sequential_plain_f64"]["seconds"] / b_s, 3)
+    for lat in lats:
+        lat.close()
+    return out
 
 
 MS_SHIFTS = (0.0, 0.0005, 0.005, 0.05)
@@ -884,7 +964,8 @@ def _solve_row(lat, x, b, alg, sp, pp, budget):
                    prec_precond=pp, raise_on_error=False)
     return {k: (float(f"{v:.4g}") if isinstance(v, float) else v) for k, v in st.items()
             if k in ("status", "iters", "restarts", "reliable_updates", "true_rel_resid", "seconds",
-                     "precond", "precond_reduction", "precond_calls", "dslash_calls")}
+                     "precond", "precond_reduction", "precond_rate", "precond_switches", "precond_calls",
+                     "dslash_calls")}
 
 
 def measure_ptc(dirac, synth, dev, stream):
@@ -975,10 +1056,13 @@ def run_solves(dirac, synth, U, src, dev):
         net.set_weights(w)
         res["ptc_apply"] = ptc_apply_rates(lat, net, lat.to_device(src, dirac.F32), torch.cuda.current_stream(),
                                            DIMS)
-        for name, force, pp in (("gcr_ptc_mixed", True, dirac.F32), ("gcr_ptc_select_mixed", False, dirac.F16)):
+        # forced network (FP32 Krylov space, as the network's layers); adaptive choice between
+        # the network and the FP16 Schwarz preconditioner with the FP16 Krylov space of GCR-DD
+        for name, force, sp, pp in (("gcr_ptc_mixed", True, dirac.F32, dirac.F32),
+                                    ("gcr_ptc_select_mixed", False, dirac.F16, dirac.F16)):
             net.attach(force=force)
             torch.cuda.synchronize()
-            res[name] = _solve_row(lat, x, b, dirac.GCR_PTC, dirac.F32, pp, gcr_budget)
+            res[name] = _solve_row(lat, x, b, dirac.GCR_PTC, sp, pp, gcr_budget)
             res[name]["trained_on"] = rep
         for alg in ("gcr_dd", "bicgstab", "bicgstab_eo", "gcr_ptc", "gcr_ptc_select"):
             a, b_ = res.get(f"{alg}_mixed"), res.get(f"{alg}_f64") or res.get("gcr_dd_f64")

@@ -120,6 +120,19 @@ int dirac_apply(dirac_ctx* ctx, void* out, const void* in, dirac_parity parity, 
  * (parity form: D^dagger = -D). */
 int dirac_apply_dagger(dirac_ctx* ctx, void* out, const void* in, dirac_parity parity,
                        dirac_prec prec, void* stream);
+/* The Wilson-clover M (dagger = 1: M^dagger) on FP64 full fields, evaluated in
+ * double-single arithmetic (pairs of binary32 values, about 48 significant bits; the
+ * sum and product steps are exact error-free transformations): agrees with the FP64
+ * dirac_apply to ~1e-14 relative and runs on the FP32 pipes. When switched on, solve()
+ * uses it for the FP64 true residuals of its restarts and reliable updates (Sec. 8.2 keeps
+ * only those, the solution and the global sums above the sloppy precision); a residual it
+ * finds below the tolerance, and the final residual of every solve, are recomputed with
+ * the FP64 operator. DIRAC_ERR_UNSUPPORTED unless Wilson-clover with 18-real FP64 links.
+ * dirac_set_ds_residual(ctx, 1) makes solve() and solve_batched() use it for those
+ * residuals; the default (0) is the FP64 operator throughout, which measured faster. */
+int dirac_apply_ds(dirac_ctx* ctx, void* out, const void* in, int dagger, void* stream);
+int dirac_set_ds_residual(dirac_ctx* ctx, int on);
+
 /* Normal operator M^dagger M. FULL: whole lattice (both kinds). EVEN/ODD: asqtad
  * only, (M^dagger M)_pp = m^2 - 1/4 D_{p,1-p} D_{1-p,p} on a half-field (Sec. 3.1:
  * the staggered normal matrix decouples the parities). */
@@ -155,6 +168,20 @@ int dirac_batch_capture(dirac_batch* plan, int napply, void* stream);
 int dirac_batch_info(const dirac_batch* plan, int* rhs_per_cta, int* ctas_per_sm, int* grid,
                      double* tuned_ms);
 int dirac_batch_destroy(dirac_batch* plan);
+/* Tensor-core form of the batched operator, for FP16 storage with 12- or 18-real links
+ * (not in the paper: a multi-right-hand-side extension). Per site the link-times-
+ * spinor products of all right-hand sides of a tile are one dense contraction (Eq. 2:
+ * rows = right-hand sides, K = 8 spin-projected hops x 3 colours, columns = colour) run
+ * with FP16 operands and FP32 accumulation on the tensor cores, the clover blocks as a
+ * fourth k-tile; results agree with dirac_apply in FP16 within the FP16 per-site bound,
+ * not bit for bit. dirac_batch_create times it beside the CUDA-core kernel and keeps the
+ * faster one. dirac_batch_set_tensor_cores selects it (1) or the CUDA-core kernel (0);
+ * DIRAC_ERR_UNSUPPORTED when the plan has no tensor-core form; a captured graph is
+ * dropped (capture again). dirac_batch_kernel_info reports the kernel in use and the
+ * creation timings in ms (-1: not timed). */
+int dirac_batch_set_tensor_cores(dirac_batch* plan, int on);
+int dirac_batch_kernel_info(const dirac_batch* plan, int* tensor_cores, double* cuda_core_ms,
+                            double* tensor_core_ms);
 
 /* out = K in: the non-overlapping additive Schwarz preconditioner of Sec. 3.2 / 8.1
  * for the Wilson-clover operator. On every block (params.block) the operator with
@@ -237,8 +264,12 @@ typedef struct {
   double true_rel_resid;   /* final ||b - A x|| / ||b|| recomputed in FP64 */
   double seconds;          /* wall time of the solve including the final sync */
   double flops;            /* operator + preconditioner + BLAS flops from per-site counts */
-  int precond_kind;        /* preconditioner used: 0 none, 1 Schwarz, 2 PTC network */
-  double precond_reduction[2]; /* GCR_PTC: ||r0 - M K r0|| / ||r0|| of K = Schwarz, PTC */
+  int precond_kind;        /* preconditioner of the last cycle: 0 none, 1 Schwarz, 2 PTC */
+  double precond_reduction[2]; /* GCR_PTC: ||r0 - M K r0|| / ||r0|| of K = Schwarz, PTC (the
+                                  test that picks the first cycle's preconditioner) */
+  double precond_rate[2];  /* GCR_PTC: last measured residual reduction per second
+                              (ln ||r|| per second) of K = Schwarz, PTC; -1 if never run */
+  int precond_switches;    /* GCR_PTC: changes of preconditioner at restarts */
 } dirac_solver_stats;
 
 /* Solve A x = b in FP64 (A = M, M^dagger M or (M^dagger M)_ee per alg). x and b are
@@ -247,6 +278,23 @@ typedef struct {
  * DIRAC_ERR_NOT_CONVERGED when max_iter ran out (x = last iterate, stats filled). */
 int solve(dirac_ctx* ctx, void* x, const void* b, const dirac_solver_params* params,
           dirac_solver_stats* stats, void* stream);
+
+/* Batched solves (not in the paper: the multi-right-hand-side extension of solve):
+ * M_l x_{l,r} = b_{l,r} for r < nrhs[l] on nlat (1..16) Wilson-clover lattices of any
+ * sizes, at most 256 right-hand sides in all. x[l] and b[l] hold nrhs[l] consecutive
+ * FP64 full fields (caller-owned device memory; x is read as the initial guess iff
+ * params->use_x0). Every right-hand side runs its own BiCGstab (params->alg must be
+ * DIRAC_SOLVER_BICGSTAB) with reliable updates every params->delta in
+ * params->prec_sloppy, to params->tol; one iteration of all of them is one batched
+ * operator application per BiCGstab operator step (the tensor-core kernel for FP16),
+ * single BLAS launches over all right-hand sides and a replayed CUDA graph. A converged
+ * right-hand side stops changing while the others continue. stats: one entry per
+ * right-hand side (lattice-major): its iterations, reliable updates and final FP64 true
+ * residual; seconds is the wall time of the whole call. Returns DIRAC_ERR_NOT_CONVERGED
+ * (or BREAKDOWN / NONFINITE) if some right-hand side did not reach tol; the others keep
+ * their solutions. Synchronises stream. */
+int solve_batched(dirac_ctx* const* ctxs, int nlat, void* const* x, const void* const* b, const int* nrhs,
+                  const dirac_solver_params* params, dirac_solver_stats* stats, void* stream);
 
 /* Multi-shift solve of Eq. 4, (M^dagger M + sigma_j) x_j = b for j < nshift (1..16,
  * sigma_j >= 0), the strategy of Sec. 8.2: a multi-shift CG in params->prec_sloppy
@@ -328,10 +376,12 @@ int dirac_ptc_set_tensor_cores(dirac_ptc* net, int on);
  * (dirac_ptc_set_tensor_cores clears the error). stall = 0 restores normal operation. */
 int dirac_ptc_test_stall(dirac_ptc* net, int stall, double wait_seconds);
 /* Make net the preconditioner of DIRAC_SOLVER_GCR_PTC on ctx (NULL detaches). With
- * force = 0, every such solve starts by applying both the network and the Schwarz
- * preconditioner to the initial residual r0 and keeps the one with the smaller
- * ||r0 - M K r0|| (Schwarz is the fallback); force = 1 always uses the network. stats
- * report the choice and, with force = 0, both reductions. */
+ * force = 0, every such solve starts with whichever of the network and the Schwarz
+ * preconditioner gives the smaller ||r0 - M K r0||, runs the other one for one restart
+ * cycle, and from then on each cycle uses the preconditioner with the higher measured
+ * residual reduction per second of its last cycle (Schwarz is the fallback); force = 1
+ * always uses the network. stats report the one-step reductions, the measured rates, the
+ * switches and the preconditioner of the last cycle. */
 int dirac_ptc_attach(dirac_ctx* ctx, dirac_ptc* net, int force);
 /* Free the network (detaching it first). NULL is a no-op. */
 int dirac_ptc_destroy(dirac_ptc* net);

@@ -190,6 +190,30 @@ int apply_op(dirac_ctx* c, char* out, const char* in, int parity, int prec, int 
   return DIRAC_OK;
 }
 
+void launch_wilson_ds(const WilsonArg& a, cudaStream_t st);
+
+bool ds_available(const dirac_ctx* c) {
+  return c->p.kind == DIRAC_WILSON_CLOVER && c->p.recon[P64] == 18 && c->gauge[P64] != nullptr &&
+         (c->p.csw == 0.0 || c->clover[P64] != nullptr);
+}
+
+int wilson_M_ds(dirac_ctx* c, char* out, const char* in, bool dag, cudaStream_t st) {
+  if (!ds_available(c))
+    return set_err(c, DIRAC_ERR_UNSUPPORTED, "double-single operator: Wilson-clover with 18-real FP64 links");
+  WilsonArg a;
+  const size_t hb = spinor_half_bytes(P64, 24, c->Vh);
+  a.out[0] = out; a.out[1] = out + hb;
+  a.in[0] = in; a.in[1] = in + hb;
+  a.gauge = c->gauge[P64];
+  a.clover = c->p.csw != 0.0 ? c->clover[P64] : nullptr;
+  a.g = c->g;
+  a.kappa = c->p.kappa;
+  a.dagger = dag;
+  a.out_parity = 0;
+  launch_wilson_ds(a, st);
+  return cuda_check(c, "double-single wilson M kernel");
+}
+
 int schwarz_apply(dirac_ctx* c, char* out, const char* in, int prec, cudaStream_t st) {
   int rc = launch_schwarz(prec, c->p.recon[prec], out, in, c->gauge[prec], c->clover[prec], c->g,
                           c->p.block, c->p.mr_steps, c->p.kappa, st);
@@ -407,6 +431,19 @@ int dirac_apply_dagger(dirac_ctx* c, void* out, const void* in, dirac_parity par
                        void* stream) {
   return apply_entry(c, out, in, parity, prec, 1, stream);
 }
+int dirac_apply_ds(dirac_ctx* c, void* out, const void* in, int dagger, void* stream) {
+  int rc = check_op(c, P64, false);
+  if (rc) return rc;
+  if (!out || !in || out == in) return set_err(c, DIRAC_ERR_ARG, "bad field pointers");
+  return wilson_M_ds(c, (char*)out, (const char*)in, dagger != 0, (cudaStream_t)stream);
+}
+
+int dirac_set_ds_residual(dirac_ctx* c, int on) {
+  if (!c) return DIRAC_ERR_ARG;
+  c->ds_residual = on != 0;
+  return DIRAC_OK;
+}
+
 int dirac_apply_normal(dirac_ctx* c, void* out, const void* in, dirac_parity parity, dirac_prec prec,
                        void* stream) {
   return apply_entry(c, out, in, parity, prec, 2, stream);

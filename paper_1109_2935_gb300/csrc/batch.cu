@@ -7,12 +7,16 @@
 // from L1. Every output site runs the same stencil code as the single-RHS kernel, so
 // results are bitwise identical. The tile shape (RG and the number of resident CTAs)
 // is chosen per batch plan by timing the candidates once (the autotuner below), and a
-// plan can record its launches in a CUDA graph for replay.
+// plan can record its launches in a CUDA graph for replay. With FP16 storage the plan
+// also times the tensor-core kernel of mrhs_tc.cu (all right-hand sides of a site in
+// one dense contraction) and keeps the faster of the two.
 #include <cmath>
 #include <string>
 #include <vector>
 
 #include "internal.h"
+#include "mrhs_tc.h"
+#include "wilson_ds.cuh"
 #include "wilson.cuh"
 
 namespace dirac {
@@ -77,6 +81,18 @@ __global__ void __launch_bounds__(kTileSites * kMaxRG, 1)
   }
 }
 
+// the double-single form (FP64 fields): 4 right-hand sides per CTA (the untimed default
+// shape), so that a thread may hold the float-float values in up to 255 registers
+__global__ void __launch_bounds__(kTileSites * 4, 1)
+    batch_kernel_ds(const BatchLat* __restrict__ lats, int nlat, int ntiles) {
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    int l = 0;
+    while (l + 1 < nlat && t >= lats[l + 1].tile_begin) ++l;
+    const BatchLat L = lats[l];
+    batch_tile<P64DS, 18>(L, t - L.tile_begin, 4);
+  }
+}
+
 template <int PREC>
 static void launch_mrhs_prec(int recon, const BatchLat& L, int RG, int grid, cudaStream_t st) {
   dim3 block(kTileSites, RG);
@@ -135,12 +151,19 @@ struct dirac_batch {
   std::vector<BatchLat> lats;    // host copy (RG-dependent fields refreshed by the tuner)
   BatchLat* d_lats = nullptr;    // device table
   int prec = 0, recon = 12, ntiles = 0;
+  bool ds = false;               // FP64 fields: double-single arithmetic (18-real links)
   int RG = 1, per_sm = 1, grid = 1;
   double tuned_ms = 0;
   std::vector<double> cand_ms;   // autotuner timings, candidate order
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   int graph_napply = 0;
+  // tensor-core kernel (FP16 storage): its lattice table, grid and creation timing
+  bool use_tc = false;
+  TcLat* d_tc = nullptr;
+  std::vector<int*> tc_nbr;      // per-lattice neighbour tables of the tensor-core kernel
+  int tc_ntiles = 0, tc_grid = 0;
+  double tc_ms = -1, cc_ms = -1;
   std::string err;
 };
 
@@ -148,6 +171,7 @@ namespace dirac {
 
 // the tile-shape candidates: (right-hand sides per CTA, resident CTAs per SM)
 static const int kCand[][2] = {{1, 16}, {2, 8}, {4, 4}, {8, 2}, {16, 1}, {2, 16}, {4, 8}, {8, 4}};
+static constexpr int kDefaultCand = 2;  // the shape the full tuning picks on the batched workloads
 
 static int batch_layout(dirac_batch* b, int RG, cudaStream_t st) {
   int begin = 0;
@@ -170,7 +194,13 @@ static int batch_layout(dirac_batch* b, int RG, cudaStream_t st) {
 
 static void batch_launch_direct(dirac_batch* b, cudaStream_t st) {
   const int nlat = (int)b->lats.size();
-  if (b->prec == P64) launch_batch_prec<P64>(b->recon, b->d_lats, nlat, b->ntiles, b->RG, b->grid, st);
+  if (b->use_tc) {
+    launch_mrhs_tc(b->recon, b->d_tc, nlat, b->tc_ntiles, b->tc_grid, st);
+    return;
+  }
+  if (b->prec == P64 && b->ds)
+    batch_kernel_ds<<<b->grid, dim3(kTileSites, 4), 0, st>>>(b->d_lats, nlat, b->ntiles);
+  else if (b->prec == P64) launch_batch_prec<P64>(b->recon, b->d_lats, nlat, b->ntiles, b->RG, b->grid, st);
   else if (b->prec == P32) launch_batch_prec<P32>(b->recon, b->d_lats, nlat, b->ntiles, b->RG, b->grid, st);
   else launch_batch_prec<P16>(b->recon, b->d_lats, nlat, b->ntiles, b->RG, b->grid, st);
 }
@@ -201,6 +231,15 @@ int dirac_apply_multi(dirac_ctx* c, void* out, const void* in, int nrhs, dirac_p
 
 int dirac_batch_create(dirac_ctx* const* ctxs, int nlat, void* const* out, const void* const* in,
                        const int* nrhs, dirac_prec prec, void* stream, dirac_batch** plan) {
+  return dirac::batch_create(ctxs, nlat, out, in, nrhs, prec, (cudaStream_t)stream, plan, 2, false);
+}
+
+}  // extern "C"
+
+namespace dirac {
+
+int batch_create(dirac_ctx* const* ctxs, int nlat, void* const* out, const void* const* in, const int* nrhs,
+                 int prec, cudaStream_t stream, dirac_batch** plan, int tune, bool ds) {
   if (!ctxs || !out || !in || !nrhs || !plan || nlat < 1 || nlat > kMaxLat) return DIRAC_ERR_ARG;
   *plan = nullptr;
   int recon = -1;
@@ -214,9 +253,12 @@ int dirac_batch_create(dirac_ctx* const* ctxs, int nlat, void* const* out, const
       return set_err(c, DIRAC_ERR_ARG, "batch: every lattice needs the same link compression");
     recon = c->p.recon[prec];
   }
+  if (ds && (prec != P64 || recon != 18 || tune != 0))
+    return set_err(ctxs[0], DIRAC_ERR_UNSUPPORTED, "batch: double-single needs FP64 18-real links, untimed");
   dirac_batch* b = new dirac_batch();
   b->prec = prec;
   b->recon = recon;
+  b->ds = ds;
   for (int l = 0; l < nlat; ++l) {
     b->ctxs.push_back(ctxs[l]);
     b->lats.push_back(describe(ctxs[l], prec, in[l], out[l], nrhs[l], 1));
@@ -228,7 +270,7 @@ int dirac_batch_create(dirac_ctx* const* ctxs, int nlat, void* const* out, const
   }
   // autotune: time every candidate shape once (after one warm-up launch) and keep the
   // fastest; the launches write the plan's outputs, which the caller owns anyway
-  cudaStream_t st = (cudaStream_t)stream;
+  cudaStream_t st = stream;
   int max_rhs = 1;
   for (int l = 0; l < nlat; ++l) max_rhs = nrhs[l] > max_rhs ? nrhs[l] : max_rhs;
   cudaEvent_t e0, e1;
@@ -239,7 +281,18 @@ int dirac_batch_create(dirac_ctx* const* ctxs, int nlat, void* const* out, const
   const int ncand = (int)(sizeof(kCand) / sizeof(kCand[0]));
   for (int k = 0; k < ncand; ++k) {
     const int RG = kCand[k][0], per_sm = kCand[k][1];
-    if (RG > max_rhs && RG > 1) { b->cand_ms.push_back(-1); continue; }
+    // tune < 2: only the shape (4 right-hand sides per CTA, 4 CTAs per SM)
+    // (the default shape also serves plans with fewer right-hand sides: idle warps exit)
+    if ((tune == 2 && RG > max_rhs && RG > 1) || (tune < 2 && k != kDefaultCand)) {
+      b->cand_ms.push_back(-1);
+      continue;
+    }
+    if (tune == 0) {  // no timing at all
+      best = 0;
+      bi = k;
+      b->cand_ms.push_back(-1);
+      continue;
+    }
     b->RG = RG;
     if (batch_layout(b, RG, st)) break;
     b->grid = grid_for(per_sm, b->ntiles);
@@ -273,9 +326,78 @@ int dirac_batch_create(dirac_ctx* const* ctxs, int nlat, void* const* out, const
   }
   b->grid = grid_for(b->per_sm, b->ntiles);
   b->tuned_ms = best;
+  b->cc_ms = best;
+  // the tensor-core kernel (FP16 storage, 12- or 18-real links): timed the same way; the
+  // plan keeps whichever kernel is faster
+  if (prec == DIRAC_PREC_F16 && (recon == 12 || recon == 18)) {
+    std::vector<TcLat> tl(nlat);
+    int begin = 0;
+    for (int l = 0; l < nlat; ++l) {
+      const BatchLat& L = b->lats[l];
+      TcLat& T = tl[l];
+      T.g = L.g;
+      T.gauge = L.gauge;
+      T.clover = L.clover;
+      T.kappa = (float)L.kappa;
+      T.in = L.in;
+      T.out = L.out;
+      T.field_bytes = L.field_bytes;
+      T.nrhs = L.nrhs;
+      T.ctiles = tc_ctiles(L.g.Vh);
+      T.tiles = tc_tiles(T);
+      T.tile_begin = begin;
+      int* nb = nullptr;
+      if (tc_build_nbr(L.g, &nb, st) == DIRAC_OK) b->tc_nbr.push_back(nb);
+      T.nbr = nb;
+      begin += T.tiles;
+    }
+    b->tc_ntiles = begin;
+    const long g = (long)sm_count() * tc_ctas_per_sm(recon);
+    b->tc_grid = (int)(g < begin ? g : begin);
+    bool tables = true;
+    for (int l = 0; l < nlat; ++l) tables = tables && tl[l].nbr != nullptr;
+    if (!tables || cudaMalloc(&b->d_tc, sizeof(TcLat) * nlat) != cudaSuccess ||
+        cudaMemcpyAsync(b->d_tc, tl.data(), sizeof(TcLat) * nlat, cudaMemcpyHostToDevice, st) != cudaSuccess) {
+      cudaGetLastError();
+      if (b->d_tc) cudaFree(b->d_tc);
+      b->d_tc = nullptr;
+    } else if (tune == 0) {
+      b->use_tc = true;  // untimed plans take the tensor-core kernel where there is one
+    } else {
+      cudaEvent_t f0, f1;
+      cudaEventCreate(&f0);
+      cudaEventCreate(&f1);
+      b->use_tc = true;
+      batch_launch_direct(b, st);
+      cudaEventRecord(f0, st);
+      for (int r = 0; r < 3; ++r) batch_launch_direct(b, st);
+      cudaEventRecord(f1, st);
+      float ms = 0;
+      if (cudaEventSynchronize(f1) == cudaSuccess && cudaGetLastError() == cudaSuccess &&
+          cudaEventElapsedTime(&ms, f0, f1) == cudaSuccess) {
+        b->tc_ms = ms / 3;
+        b->use_tc = b->tc_ms < best;
+        if (b->use_tc) b->tuned_ms = b->tc_ms;
+      } else {
+        cudaGetLastError();
+        b->use_tc = false;
+      }
+      cudaEventDestroy(f0);
+      cudaEventDestroy(f1);
+      if (b->tc_ms < 0) {
+        // the tensor-core launch failed: the plan keeps the CUDA-core kernel
+        cudaStreamSynchronize(st);
+        cudaGetLastError();
+      }
+    }
+  }
   *plan = b;
   return cudaStreamSynchronize(st) == cudaSuccess ? DIRAC_OK : DIRAC_ERR_CUDA;
 }
+
+}  // namespace dirac
+
+extern "C" {
 
 int dirac_batch_apply(dirac_batch* b, void* stream) {
   if (!b) return DIRAC_ERR_ARG;
@@ -326,10 +448,34 @@ int dirac_batch_info(const dirac_batch* b, int* rhs_per_cta, int* ctas_per_sm, i
   return DIRAC_OK;
 }
 
+int dirac_batch_set_tensor_cores(dirac_batch* b, int on) {
+  if (!b) return DIRAC_ERR_ARG;
+  if (on && !b->d_tc) return DIRAC_ERR_UNSUPPORTED;
+  if (b->use_tc != (on != 0)) {
+    // a captured graph holds the other kernel: drop it (capture again)
+    if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
+    if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
+    b->graph_napply = 0;
+  }
+  b->use_tc = on != 0;
+  b->tuned_ms = b->use_tc ? b->tc_ms : b->cc_ms;
+  return DIRAC_OK;
+}
+
+int dirac_batch_kernel_info(const dirac_batch* b, int* tensor_cores, double* cuda_core_ms, double* tensor_core_ms) {
+  if (!b) return DIRAC_ERR_ARG;
+  if (tensor_cores) *tensor_cores = b->use_tc ? 1 : 0;
+  if (cuda_core_ms) *cuda_core_ms = b->cc_ms;
+  if (tensor_core_ms) *tensor_core_ms = b->tc_ms;
+  return DIRAC_OK;
+}
+
 int dirac_batch_destroy(dirac_batch* b) {
   if (!b) return DIRAC_ERR_ARG;
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
+  if (b->d_tc) cudaFree(b->d_tc);
+  for (int* t : b->tc_nbr) cudaFree(t);
   if (b->d_lats) cudaFree(b->d_lats);
   delete b;
   cudaGetLastError();

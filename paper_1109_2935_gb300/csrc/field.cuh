@@ -12,6 +12,9 @@
 namespace dirac {
 
 enum { P64 = 0, P32 = 1, P16 = 2 };
+// a fourth arithmetic for stencils only: FP64 storage read into double-single (float-float)
+// arithmetic (dsfloat.cuh, wilson_ds.cu); fields and storage are those of P64
+enum { P64DS = 3 };
 
 template <int PREC> struct Real { using T = float; };
 template <> struct Real<P64> { using T = double; };

@@ -135,11 +135,23 @@ int ensure_tmp(dirac_ctx* c, int prec);
 int apply_op(dirac_ctx* c, char* out, const char* in, int parity, int prec, int which, cudaStream_t st,
              double shift = 0.0);
 int schwarz_apply(dirac_ctx* c, char* out, const char* in, int prec, cudaStream_t st);
+// the Wilson-clover M (dag: M^dagger) on FP64 full fields in double-single arithmetic
+// (wilson_ds.cu); DIRAC_ERR_UNSUPPORTED unless Wilson-clover with 18-real FP64 links
+int wilson_M_ds(dirac_ctx* c, char* out, const char* in, bool dag, cudaStream_t st);
+bool ds_available(const dirac_ctx* c);
 // even-odd form (Wilson-clover): bhat_e = b_e + kappa D_eo Ahat_oo^-1 b_o and
 // x_o = Ahat_oo^-1 (b_o + kappa D_oe x_e); which = 3 / 4 in apply_op is the Schur
 // operator / its adjoint on even half-fields
 int schur_source(dirac_ctx* c, char* bhat, const char* b, int prec, cudaStream_t st);
 int schur_reconstruct(dirac_ctx* c, char* x, const char* b, int prec, cudaStream_t st);
+
+// ---------------------------------------------------------------- batched operator (batch.cu)
+// dirac_batch_create with a tuning level: 2 = every tile shape and the tensor-core kernel
+// timed (the public call), 1 = the default shape timed against the tensor-core kernel,
+// 0 = no timing (default shape; the tensor-core kernel where it exists)
+// (ds: FP64 fields, 18-real links, arithmetic in double-single as dirac_apply_ds)
+int batch_create(dirac_ctx* const* ctxs, int nlat, void* const* out, const void* const* in, const int* nrhs,
+                 int prec, cudaStream_t stream, dirac_batch** plan, int tune, bool ds = false);
 
 // ---------------------------------------------------------------- PTC network (ptc.cu)
 // out = K in on FP32 full fields; flops of one application; free a network
@@ -191,5 +203,9 @@ struct dirac_ctx {
   // orders it after the caller's stream
   cudaStream_t solve_stream = nullptr;
   cudaEvent_t solve_event = nullptr;
+  // solve(): FP64 true residuals of restarts / reliable updates in double-single arithmetic
+  // (the final check and any convergence decision are confirmed in FP64). Off by default:
+  // measured slower than the FP64 operator on this part (dirac_set_ds_residual)
+  int ds_residual = 0;
   std::string err;
 };

@@ -330,17 +330,41 @@ int flag_error(Ctx& S, int fl, const char* who) {
 // 11-bit resolution of the accumulated correction and be lost.
 int accum_prec(int sp) { return sp == P16 ? P32 : sp; }
 
-// r = b - A x in FP64, returns ||r||^2 (host, synchronising)
-int true_residual(Ctx& S, char* r, const char* x, const char* b, double* rr) {
+// A x for the true residual: FP64 fields; for the Wilson-clover M (or M^dagger M) on the
+// whole lattice the operator runs in double-single arithmetic unless switched off
+// (dirac_set_ds_residual), otherwise in FP64
+int residual_operator(Ctx& S, char* out, const char* x, bool* ds) {
+  dirac_ctx* c = S.c;
+  *ds = c->ds_residual && S.parity < 0 && (S.which == 0 || S.which == 2) && ds_available(c);
+  if (!*ds) return S.A(out, x, P64);
+  S.stats->dslash_calls += 1;
+  S.stats->flops += S.flops_per_apply;
+  if (S.which == 0) return wilson_M_ds(c, out, x, false, S.st);
+  TRY(ensure_tmp(c, P64));
+  TRY(wilson_M_ds(c, c->tmp[P64], x, false, S.st));
+  TRY(wilson_M_ds(c, out, c->tmp[P64], true, S.st));
+  if (S.shift != 0.0) BT(blas_axpby(c->blas, cval(S.shift), S.f(x, P64), cval(1), S.f(out, P64), S.st));
+  return DIRAC_OK;
+}
+
+// r = b - A x in FP64 storage, returns ||r||^2 (host, synchronising). A residual that the
+// double-single operator puts below `target` (a convergence decision) is recomputed with
+// the FP64 operator, which then decides.
+int true_residual(Ctx& S, char* r, const char* x, const char* b, double* rr, double target = -1.0) {
   Range range("true residual (FP64)");
-  TRY(S.A(r, x, P64));
+  bool ds = false;
+  TRY(residual_operator(S, r, x, &ds));
   BT(blas_xmy_norm(S.c->blas, S.f(b, P64), S.f(r, P64), rr, S.st));
+  if (ds && *rr < target) {
+    TRY(S.A(r, x, P64));
+    BT(blas_xmy_norm(S.c->blas, S.f(b, P64), S.f(r, P64), rr, S.st));
+  }
   return DIRAC_OK;
 }
 
 int start_residual(Ctx& S, char* x, const char* b, char* r, const dirac_solver_params& P, double bb,
                    double* rr) {
-  if (P.use_x0) return true_residual(S, r, x, b, rr);
+  if (P.use_x0) return true_residual(S, r, x, b, rr, P.tol * P.tol * bb);
   BT(blas_zero(S.c->blas, S.f(x, P64), S.st));
   BT(blas_copy(S.c->blas, S.f(r, P64), S.f(b, P64), S.st));
   *rr = bb;
@@ -391,7 +415,7 @@ int solve_cg(Ctx& S, char* x, const char* b, const dirac_solver_params& P) {
         // reliable update: fold the sloppy correction into x, recompute r in FP64
         BT(blas_axpby(B, cval(1), S.f(xs, ap), cval(1), S.f(x, P64), S.st));
         BT(blas_zero(B, S.f(xs, ap), S.st));
-        TRY(true_residual(S, r, x, b, &rr));
+        TRY(true_residual(S, r, x, b, &rr, target));
         S.stats->reliable_updates++;
         if (rr < target) { converged = true; break; }
         BT(blas_copy(B, S.f(rs, sp), S.f(r, P64), S.st));
@@ -523,7 +547,7 @@ int solve_bicgstab(Ctx& S, char* x, const char* b, const dirac_solver_params& P)
       if ((d2 > 0 && rp < d2 * rmax) || rp < target) {
         BT(blas_axpby(B, cval(1), S.f(xs, ap), cval(1), S.f(x, P64), S.st));
         BT(blas_zero(B, S.f(xs, ap), S.st));
-        TRY(true_residual(S, r, x, b, &rr));
+        TRY(true_residual(S, r, x, b, &rr, target));
         S.stats->reliable_updates++;
         if (rr < target) { converged = true; break; }
         BT(blas_copy(B, S.f(rs, sp), S.f(r, P64), S.st));
@@ -660,10 +684,20 @@ int solve_gcr(Ctx& S, char* x, const char* b, const dirac_solver_params& P, int 
     KC((k_mirror<<<1, 1, 0, S.st>>>(S.S, S_RH, S.mirror, k & 1, k)));
     return DIRAC_OK;
   };
-  StepGraphs cap(kmax, S.graphs);
+  // Each preconditioner has its own captured steps. With K_SELECT (not forced) the choice
+  // is revisited at every restart: the residual reduction per second of the cycle just
+  // finished (natural log of ||r|| per second of wall time) is kept per preconditioner;
+  // the other one is tried once, and afterwards whichever has the higher last measured
+  // rate runs the next cycle (flexible GCR admits a change of K at a restart).
+  StepGraphs cap_n(kmax, S.graphs), cap_s(kmax, S.graphs), cap_p(kmax, S.graphs);
+  StepGraphs* caps[3] = {&cap_n, &cap_s, &cap_p};
+  const bool adaptive = precond == K_SELECT && !S.c->ptc_force;
+  double rate[3] = {-1.0, -1.0, -1.0};
+  auto cycle_t0 = std::chrono::steady_clock::now();
+  double cycle_r0 = r0n2;
   int k = 0;
   while (r0n2 > target && S.stats->iters < P.max_iter) {
-    TRY(cap.run(S, k, [&] { return step(k); }));
+    TRY(caps[kind]->run(S, k, [&] { return step(k); }));
     TRY(S.mark(k));
     ++k;
     S.stats->iters++;
@@ -688,13 +722,28 @@ int solve_gcr(Ctx& S, char* x, const char* b, const dirac_solver_params& P, int 
         xs[i] = S.f(pv[i], sp);
       }
       BT(blas_multi_caxpy(B, k, cf.data(), xs.data(), S.f(x, P64), S.st));
-      TRY(true_residual(S, r, x, b, &r0n2));
+      TRY(true_residual(S, r, x, b, &r0n2, target));
       if (!finite(r0n2)) return set_err(S.c, DIRAC_ERR_NONFINITE, "GCR: non-finite true residual");
       BT(blas_copy(B, S.f(rh, sp), S.f(r, P64), S.st));
       S.stats->restarts++;
       k = 0;
+      if (adaptive) {
+        const auto now = std::chrono::steady_clock::now();
+        const double secs = std::chrono::duration<double>(now - cycle_t0).count();
+        if (secs > 0 && r0n2 > 0 && cycle_r0 > 0) rate[kind] = 0.5 * std::log(cycle_r0 / r0n2) / secs;
+        const int other = kind == K_SCHWARZ ? K_PTC : K_SCHWARZ;
+        if (rate[other] < 0 || rate[other] > rate[kind]) {
+          kind = other;
+          S.stats->precond_switches++;
+        }
+        S.stats->precond_rate[0] = rate[K_SCHWARZ];
+        S.stats->precond_rate[1] = rate[K_PTC];
+        cycle_t0 = now;
+        cycle_r0 = r0n2;
+      }
     }
   }
+  S.stats->precond_kind = kind;
   return DIRAC_OK;
 }
 
@@ -919,6 +968,7 @@ extern "C" int solve(dirac_ctx* c, void* x, const void* b, const dirac_solver_pa
   dirac_solver_stats local{};
   dirac_solver_stats* st = stats ? stats : &local;
   *st = dirac_solver_stats{};
+  st->precond_rate[0] = st->precond_rate[1] = -1.0;
   // The solve runs on the context's own non-blocking stream, ordered after the caller's
   // stream: GCR captures its steps as CUDA graphs, which the legacy default stream
   // cannot do. The call returns after the solve finished (synchronously).

@@ -106,14 +106,14 @@ __device__ __forceinline__ void wilson_hop(C<T> acc[4][3], const T* psi, const L
 template <int PREC, typename T>
 __device__ __forceinline__ void apply_clover_site(const char* b, int Vh, int cb, const C<T> in[12],
                                                   C<T> out[12]) {
-  if constexpr (PREC == P64) {
+  if constexpr (PREC == P64 || PREC == P64DS) {
 #pragma unroll
     for (int blk = 0; blk < 2; ++blk) {
-      double v[36];
+      T v[36];
 #pragma unroll
       for (int k = 0; k < 18; ++k) {
         double2 q = ldg_chunk<double2>(b + ((size_t)(18 * blk + k) * Vh + cb) * 16);
-        v[2 * k] = q.x; v[2 * k + 1] = q.y;
+        v[2 * k] = T(q.x); v[2 * k + 1] = T(q.y);
       }
       herm6_mv<T>(v, in + 6 * blk, out + 6 * blk);
     }
@@ -147,6 +147,7 @@ __device__ __forceinline__ void apply_clover_site(const char* b, int Vh, int cb,
 template <int PREC> struct WilsonShape { static constexpr int threads = 64, minb = 10; };
 template <> struct WilsonShape<P32> { static constexpr int threads = 64, minb = 8; };
 template <> struct WilsonShape<P64> { static constexpr int threads = 128, minb = 1; };
+template <> struct WilsonShape<P64DS> { static constexpr int threads = 128, minb = 2; };
 
 // One output site of the stencil: thread index idx over the Vh (hop mode) or 2 Vh
 // (full operator) output sites. Shared by the single-RHS, multi-RHS and batched kernels.

@@ -46,11 +46,13 @@ class SolverStats(ctypes.Structure):
                 ("reliable_updates", ctypes.c_int), ("dslash_calls", ctypes.c_int),
                 ("precond_calls", ctypes.c_int), ("true_rel_resid", ctypes.c_double),
                 ("seconds", ctypes.c_double), ("flops", ctypes.c_double),
-                ("precond_kind", ctypes.c_int), ("precond_reduction", ctypes.c_double * 2)]
+                ("precond_kind", ctypes.c_int), ("precond_reduction", ctypes.c_double * 2),
+                ("precond_rate", ctypes.c_double * 2), ("precond_switches", ctypes.c_int)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}
         d["precond_reduction"] = list(self.precond_reduction)
+        d["precond_rate"] = list(self.precond_rate)
         d["precond"] = PRECOND_NAMES.get(self.precond_kind, self.precond_kind)
         return d
 
@@ -83,6 +85,8 @@ _SIGS = {
     "dirac_apply": (_ci, [_vp, _vp, _vp, _ci, _ci, _vp]),
     "dirac_apply_dagger": (_ci, [_vp, _vp, _vp, _ci, _ci, _vp]),
     "dirac_apply_normal": (_ci, [_vp, _vp, _vp, _ci, _ci, _vp]),
+    "dirac_apply_ds": (_ci, [_vp, _vp, _vp, _ci, _vp]),
+    "dirac_set_ds_residual": (_ci, [_vp, _ci]),
     "schwarz_precondition": (_ci, [_vp, _vp, _vp, _ci, _vp]),
     "dirac_apply_eo": (_ci, [_vp, _vp, _vp, _ci, _ci, _vp]),
     "dirac_apply_multi": (_ci, [_vp, _vp, _vp, _ci, _ci, _vp]),
@@ -93,6 +97,8 @@ _SIGS = {
     "dirac_batch_info": (_ci, [_vp, ctypes.POINTER(_ci), ctypes.POINTER(_ci), ctypes.POINTER(_ci),
                                ctypes.POINTER(ctypes.c_double)]),
     "dirac_batch_destroy": (_ci, [_vp]),
+    "dirac_batch_set_tensor_cores": (_ci, [_vp, _ci]),
+    "dirac_batch_kernel_info": (_ci, [_vp, ctypes.POINTER(_ci), _pd, _pd]),
     "dirac_norm2": (_ci, [_vp, _vp, _ci, _ci, _pd, _vp]),
     "dirac_cdot": (_ci, [_vp, _vp, _vp, _ci, _ci, _pd, _vp]),
     "dirac_caxpy_norm": (_ci, [_vp, _cd, _cd, _vp, _vp, _ci, _ci, _pd, _vp]),
@@ -100,6 +106,8 @@ _SIGS = {
     "solve": (_ci, [_vp, _vp, _vp, ctypes.POINTER(SolverParams), ctypes.POINTER(SolverStats), _vp]),
     "dirac_cdot_noalloc": (_ci, [_vp, _vp, _ci, _ci, ctypes.c_longlong, _ci, _vp, _vp,
                                  ctypes.c_char_p, _sz]),
+    "solve_batched": (_ci, [ctypes.POINTER(_vp), _ci, ctypes.POINTER(_vp), ctypes.POINTER(_vp),
+                            ctypes.POINTER(_ci), ctypes.POINTER(SolverParams), ctypes.POINTER(SolverStats), _vp]),
     "solve_multishift": (_ci, [_vp, ctypes.POINTER(_vp), _vp, ctypes.POINTER(ctypes.c_double), _ci,
                                ctypes.POINTER(SolverParams), ctypes.POINTER(SolverStats), _vp]),
     "dirac_ptc_create": (_ci, [_vp, ctypes.POINTER(PtcParams), ctypes.POINTER(_vp)]),
@@ -247,6 +255,14 @@ class Lattice:
         return self.check(dirac_apply_dagger(self.ctx, out.data_ptr(), inp.data_ptr(), parity,
                                              prec, _stream(stream)), "dirac_apply_dagger")
 
+    def apply_ds(self, out, inp, dagger=False, stream=None):
+        """M (or M^dagger) on FP64 full fields in double-single arithmetic."""
+        return self.check(dirac_apply_ds(self.ctx, out.data_ptr(), inp.data_ptr(), int(dagger), _stream(stream)),
+                          "dirac_apply_ds")
+
+    def set_ds_residual(self, on):
+        return self.check(dirac_set_ds_residual(self.ctx, int(on)), "dirac_set_ds_residual")
+
     def apply_normal(self, out, inp, parity=PARITY_FULL, prec=F64, stream=None):
         return self.check(dirac_apply_normal(self.ctx, out.data_ptr(), inp.data_ptr(), parity,
                                              prec, _stream(stream)), "dirac_apply_normal")
@@ -317,6 +333,24 @@ class Lattice:
                 "refine": [st[1 + j].as_dict() for j in range(n)]}
 
 
+def solve_many(lattices, xs, bs, nrhs, tol=1e-10, max_iter=10000, delta=0.1, prec_sloppy=F16,
+               use_x0=False, stream=None, raise_on_error=True):
+    """solve_batched: BiCGstab with reliable updates on nrhs[l] consecutive FP64 full fields
+    of xs[l] / bs[l] for every lattice, all right-hand sides iterated together. Returns the
+    status and one statistics dict per right-hand side (lattice-major)."""
+    n = len(lattices)
+    ctxs = (_vp * n)(*[l.ctx.value if hasattr(l.ctx, "value") else l.ctx for l in lattices])
+    xp = (_vp * n)(*[t.data_ptr() for t in xs])
+    bp = (_vp * n)(*[t.data_ptr() for t in bs])
+    r = (_ci * n)(*nrhs)
+    sp = SolverParams(BICGSTAB, tol, max_iter, 16, delta, int(use_x0), prec_sloppy, prec_sloppy)
+    st = (SolverStats * sum(nrhs))()
+    rc = solve_batched(ctxs, n, xp, bp, r, ctypes.byref(sp), st, _stream(stream))
+    if raise_on_error and rc != OK:
+        raise DiracError(rc, f"solve_batched: {dirac_last_error(lattices[0].ctx).decode()}")
+    return {"status": ERR_NAMES.get(rc, rc), "rhs": [st[j].as_dict() for j in range(sum(nrhs))]}
+
+
 class Batch:
     """A batched-operator plan over several lattices (dirac_batch_*): M of each lattice
     applied to its consecutive right-hand sides in one persistent launch."""
@@ -339,6 +373,17 @@ class Batch:
         dirac_batch_info(self.plan, ctypes.byref(rg), ctypes.byref(per), ctypes.byref(grid), ctypes.byref(ms))
         return {"rhs_per_cta": rg.value, "ctas_per_sm": per.value, "grid": grid.value,
                 "tuned_ms": ms.value}
+
+    def set_tensor_cores(self, on):
+        """Select the tensor-core kernel (FP16 storage) or the CUDA-core kernel."""
+        rc = dirac_batch_set_tensor_cores(self.plan, int(on))
+        if rc != OK:
+            raise DiracError(rc, "dirac_batch_set_tensor_cores failed")
+
+    def kernel_info(self):
+        on, cc, tc = _ci(), ctypes.c_double(), ctypes.c_double()
+        dirac_batch_kernel_info(self.plan, ctypes.byref(on), ctypes.byref(cc), ctypes.byref(tc))
+        return {"tensor_cores": bool(on.value), "cuda_core_ms": cc.value, "tensor_core_ms": tc.value}
 
     def apply(self, stream=None):
         rc = dirac_batch_apply(self.plan, _stream(stream))

@@ -65,6 +65,8 @@ def test_batch_uneven_lattices_graph(dirac, prec):
         outs.append(torch.zeros_like(xin))
         nats.append(nat)
     b = dirac.Batch(lats, outs, ins, [s[2] for s in specs], prec)
+    if prec == F16:
+        b.set_tensor_cores(False)  # the CUDA-core kernel: bitwise equal to single-RHS
     info = b.info()
     assert info["rhs_per_cta"] in (1, 2, 4, 8, 16) and info["grid"] >= 1
     for k in range(len(outs)):
@@ -128,6 +130,7 @@ def test_batch_at_the_configured_sizes(dirac):
         outs.append(torch.zeros_like(xin))
         Us.append(U)
     b = dirac.Batch(lats, outs, ins, [nrhs] * 3, prec)
+    b.set_tensor_cores(False)
     b.apply()
     torch.cuda.synchronize()
     for lat, xin, out in zip(lats, ins, outs):
@@ -136,6 +139,20 @@ def test_batch_at_the_configured_sizes(dirac):
             ref = lat.new_field(prec)
             lat.apply(ref, xin[r * fb:(r + 1) * fb], dirac.PARITY_FULL, prec)
             assert torch.equal(out[r * fb:(r + 1) * fb], ref), (lat.dims, r)
+    # the tensor-core kernel on the same plan: every output site within the FP16 per-site
+    # bound of the CUDA-core result (checked on the first and last right-hand side)
+    cc = [o.clone() for o in outs]
+    b.set_tensor_cores(True)
+    for o in outs:
+        o.zero_()
+    b.apply()
+    torch.cuda.synchronize()
+    for lat, o, c in zip(lats, outs, cc):
+        fb = lat.field_bytes(prec)
+        for r in (0, nrhs - 1):
+            got = lat.to_natural(o[r * fb:(r + 1) * fb], prec, device="cpu").numpy()
+            ref = lat.to_natural(c[r * fb:(r + 1) * fb], prec, device="cpu").numpy()
+            check(got, ref, F16, 24, f"tensor-core vs CUDA-core {lat.dims} rhs {r}")
     # the oracle on sampled sites of the last right-hand side of 32^3x64
     lat, xin, out, U = lats[-1], ins[-1], outs[-1], Us[-1]
     dims, kappa = specs[-1][0], specs[-1][1]

@@ -219,3 +219,46 @@ def test_asqtad_solves_48x144_oracle_gated(dirac):
         est = _staggered_sampled_residual(fat_n, lng_n, mass, sg, b_n, xjn, dims, seed=20 + j)
         assert est < 1e-9, (j, est)
     lat.close()
+
+
+def test_learned_preconditioner_adaptive_choice_24x128(dirac):
+    """GCR_PTC without forcing the network, on the 24^3x128 workload with a network trained
+    on 16^4 at kappa 0.135 and applied unchanged: at kappa 0.124 (where the Schwarz
+    preconditioner converges faster per second) the solve ends on Schwarz and takes at most
+    a quarter longer than GCR-DD with the same precisions; at kappa 0.1350 (where GCR-DD
+    stalls) it ends on the network and converges. Both solutions pass the oracle's sampled
+    residual."""
+    import bench
+    dims = (24, 24, 24, 128)
+    plat, pnet, _, _, _ = bench.train_ptc(dirac, synth, torch.device("cuda"), 0.135)
+    w = pnet.get_weights()
+    plat.close()
+    U = synth.wilson_gauge(dims, 0.5, 3, 2001, device="cuda")
+    b = synth.wilson_spinor(dims, 2002, device="cuda")
+    for kappa, expect in ((0.124, "schwarz"), (0.135, "ptc")):
+        lat = dirac.Lattice(dims, dirac.WILSON_CLOVER, kappa=kappa, csw=1.0, block=(4, 4, 4, 4), mr_steps=6,
+                            recon=(18, 12, 12))
+        lat.load_gauge(U)
+        net = dirac.Ptc(lat, bench.PTC_CHANNELS)
+        net.set_weights(w)
+        net.attach(force=False)
+        fb = lat.to_device(b, F64)
+        fx = lat.new_field(F64)
+        st = lat.solve(fx, fb, dirac.GCR_PTC, tol=1e-10, max_iter=3000, k_max=16, delta=0.1,
+                       prec_sloppy=F16, prec_precond=F16)
+        info = {k: st[k] for k in ("iters", "seconds", "precond", "precond_rate", "precond_switches",
+                                   "precond_reduction", "true_rel_resid")}
+        assert st["true_rel_resid"] <= 1e-10, info
+        assert st["precond_rate"][0] != -1 and st["precond_rate"][1] != -1, info  # both were measured
+        if kappa == 0.124:
+            fy = lat.new_field(F64)
+            ref = lat.solve(fy, fb, dirac.GCR_DD, tol=1e-10, max_iter=3000, k_max=16, delta=0.1,
+                            prec_sloppy=F16, prec_precond=F16)
+            assert st["seconds"] <= 1.25 * ref["seconds"], (info, ref["seconds"])
+        else:
+            assert st["precond"] == expect, info
+        x = lat.to_natural(fx, F64, device="cpu").numpy()
+        est = _sampled_residual(U.cpu().numpy(), 1.0, kappa, b.cpu().numpy(), x, dims)
+        assert est < 1e-9, est
+        net.close()
+        lat.close()
