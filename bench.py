@@ -472,6 +472,8 @@ def main():
         rows["batched_multi_rhs"] = measure_batch(dirac, synth, dev, stream, peak)
         if not args.no_solve:
             rows["batched_solves"] = measure_batched_solves(dirac, synth, dev)
+            rows["batched_solves_small_lattices"] = measure_batched_solves(dirac, synth, dev, BATCH_SMALL,
+                                                                           BATCH_SMALL_RHS)
     if not args.no_ptc and not args.no_solve:
         rows["ptc_preconditioner"] = measure_ptc(dirac, synth, dev, stream)
     if not args.no_asqtad:
@@ -659,29 +661,39 @@ def measure_batch_prec(dirac, synth, dev, stream, peak, prec):
     return res
 
 
-def measure_batched_solves(dirac, synth, dev):
+# many small lattices (launch-latency territory for one-at-a-time solves)
+BATCH_SMALL = (((8, 8, 8, 8), 0.130, 6001), ((8, 8, 8, 12), 0.131, 6003), ((12, 12, 12, 12), 0.132, 6005),
+               ((8, 8, 16, 16), 0.133, 6007), ((12, 12, 12, 16), 0.134, 6009), ((16, 16, 16, 16), 0.135, 6011),
+               ((8, 8, 8, 16), 0.136, 6013), ((12, 12, 16, 16), 0.130, 6015))
+BATCH_SMALL_RHS = 8
+
+
+def measure_batched_solves(dirac, synth, dev, lattices=None, nrhs_each=None):
     """The batched workload's 36 systems (12 right-hand sides on each lattice) solved to a
     true residual of 1e-10: all together by solve_batched (mixed FP16/FP64 BiCGstab, one
     iteration of every system at a time on the batched operator) vs the same mixed solver
     one system at a time vs plain FP64 BiCGstab one system at a time."""
     import torch
+    BATCH_LAT = BATCH_LATTICES if lattices is None else lattices
+    BATCH_RHS_N = BATCH_RHS if nrhs_each is None else nrhs_each
     lats, xs, bs = [], [], []
-    for dims, kappa, seed in BATCH_LATTICES:
+    for dims, kappa, seed in BATCH_LAT:
         U = synth.wilson_gauge(dims, 0.5, BATCH_SMEAR, seed, device=dev)
         lat = dirac.Lattice(dims, dirac.WILSON_CLOVER, kappa=kappa, csw=CSW, recon=(18, 12, 12),
                             prec_mask=(1 << dirac.F64) | (1 << dirac.F16))
         lat.load_gauge(U)
         fb = lat.field_bytes(dirac.F64)
-        b = torch.empty(BATCH_RHS * fb, dtype=torch.uint8, device=dev)
-        for r in range(BATCH_RHS):
+        b = torch.empty(BATCH_RHS_N * fb, dtype=torch.uint8, device=dev)
+        for r in range(BATCH_RHS_N):
             lat.import_spinor(b[r * fb:(r + 1) * fb], dirac.F64, -1,
                               synth.wilson_spinor(dims, seed + 100 + r, device=dev))
         lats.append(lat)
         bs.append(b)
         xs.append(torch.zeros_like(b))
     torch.cuda.synchronize()
-    nrhs = [BATCH_RHS] * len(lats)
-    out = {"systems": sum(nrhs), "tol": 1e-10, "gauge": "sigma 0.5, no smoothing"}
+    nrhs = [BATCH_RHS_N] * len(lats)
+    out = {"systems": sum(nrhs), "lattices": [list(d) for d, _, _ in BATCH_LAT], "rhs_per_lattice": BATCH_RHS_N,
+           "tol": 1e-10, "gauge": "sigma 0.5, no smoothing"}
     t0 = time.perf_counter()
     r = dirac.solve_many(lats, xs, bs, nrhs, tol=1e-10, max_iter=4000, delta=0.1, prec_sloppy=dirac.F16,
                          raise_on_error=False)
@@ -696,7 +708,7 @@ def measure_batched_solves(dirac, synth, dev):
         for lat, b in zip(lats, bs):
             fb = lat.field_bytes(dirac.F64)
             x = lat.new_field(dirac.F64)
-            for k in range(BATCH_RHS):
+            for k in range(BATCH_RHS_N):
                 torch.cuda.synchronize()
                 t1 = time.perf_counter()
                 st = lat.solve(x, b[k * fb:(k + 1) * fb], dirac.BICGSTAB, tol=1e-10, max_iter=4000, delta=delta,

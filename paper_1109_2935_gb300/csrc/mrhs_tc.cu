@@ -16,16 +16,19 @@
 //
 // A CTA works through tiles of TS sites of one parity and all right-hand sides with two
 // warp roles and two tile stages in shared memory:
-//   producers (4 warps): the tile's links (forward and backward, decoded once, stored in
-//     B-operand order), neighbour table and stored clover; then one thread per (site,
-//     right-hand side, half of the hops) gathers its neighbour spinors, projects them in
-//     binary16 arithmetic and writes the A rows. FP16 spinors carry per-site norms, so
+//   producers (6 warps): the tile's links (forward and backward, decoded once, stored in
+//     B-operand order) and stored clover; one thread per (site, right-hand side, half of
+//     the hops) gathers its neighbour spinors, projects them in binary16 arithmetic and
+//     writes the A rows. Neighbour indices come from a per-lattice table, fetched a tile
+//     ahead, so each tile costs the producers one memory round trip. FP16 spinors carry per-site norms, so
 //     each row is scaled to a common scale S (the largest norm among its terms), kept
 //     beside it;
-//   consumers (4 warps): one warp per site loads the A fragments (ldmatrix), builds the
+//   consumers (2 warps): one warp per site loads the A fragments (ldmatrix), builds the
 //     B fragments from the staged links and clover, runs 16 MMAs (12 hopping, 4 clover),
-//     re-encodes the outputs in FP16 with new per-site norms, and the 4 warps store the
-//     tile's outputs coalesced.
+//     re-encodes the outputs in FP16 with new per-site norms, and the 2 warps store the
+//     tile's outputs coalesced. (The producers' gather is the longer half of the work:
+//     measured with 4 + 4 warps, producers alone 1.20 ms, consumers alone 0.63 ms for
+//     24^3x64 with 12 right-hand sides.)
 // Named barriers hand each stage from producers to consumers and back; both roles walk
 // the same tile sequence, so every barrier has its full count.
 // Arithmetic: binary16 operands (spinor values relative to their row scale, links,
@@ -42,15 +45,14 @@ namespace tc {
 
 constexpr int TS = 8;           // sites per tile (one parity, consecutive cb)
 constexpr int NT = 256;         // threads per CTA
-constexpr int NPT = 128;        // producer threads (warps 0..3)
-constexpr int NCW = 4;          // consumer warps (4..7)
+constexpr int NPT = 192;        // producer threads (warps 0..5)
+constexpr int NCW = 2;          // consumer warps (6..7)
 constexpr int ROWS = 16;        // right-hand sides per tile (MMA rows)
 
 constexpr int NST = 2;          // tile stages in flight
 // named barriers (0 is __syncthreads)
 constexpr int BAR_FULL = 1;     // + stage: producers arrive, consumers wait
 constexpr int BAR_EMPTY = 4;    // + stage: consumers arrive, producers wait
-constexpr int BAR_PROD = 7;     // producers among themselves
 constexpr int BAR_CONS = 8;     // consumers among themselves
 // encoded outputs of site i staged in its A area: row r at byte 16 i + 80 r (12 binary16
 // pairs, then the FP32 norm): 8 sites x 4 rows of a warp fall on distinct banks
@@ -72,7 +74,6 @@ struct Stage {
   uint32_t link[TS][100];       // 96 used; the padding spreads the sites over the banks
   uint32_t craw[TS][36];
   float S[TS][ROWS];
-  int nbr[TS][8];               // neighbour checkerboard index, bit 31: boundary sign -1
 };
 struct Smem {
   Stage st[NST];
@@ -223,9 +224,33 @@ __device__ __forceinline__ void project(const uint32_t w[12], int dir, __half2 r
   }
 }
 
+// the neighbour entry of hop h (runtime) from the two int4 of a site's table row
+__device__ __forceinline__ int nbr_of(const int4& a, const int4& b, int h) {
+  const int4 v = h < 4 ? a : b;
+  const int k = h & 3;
+  return k == 0 ? v.x : (k == 1 ? v.y : (k == 2 ? v.z : v.w));
+}
+
 template <int R>
 __device__ void producer(Smem& sm, const TcLat* __restrict__ lats, int nlat, int ntiles) {
   const int tid = threadIdx.x;  // 0 .. NPT - 1
+  // every item and link of this thread belongs to site my_i of the tile; its row of the
+  // neighbour table is fetched one tile ahead, so a tile's loads all depend only on
+  // values already in registers (one memory round trip per tile)
+  const int my_i = tid & (TS - 1);
+  int4 pn0 = make_int4(0, 0, 0, 0), pn1 = make_int4(0, 0, 0, 0);
+  auto fetch = [&](int t) {
+    if (t >= ntiles) return;
+    const TcLat& L = lats[lattice_of(lats, nlat, t)];
+    const TileRef tr = tile_ref(L, t - L.tile_begin);
+    const int cb = tr.cb0 + my_i;
+    if (cb < L.g.Vh) {
+      const int4* p = reinterpret_cast<const int4*>(L.nbr + ((size_t)tr.par * L.g.Vh + cb) * 8);
+      pn0 = __ldg(p);
+      pn1 = __ldg(p + 1);
+    }
+  };
+  fetch(blockIdx.x);
   int it = 0;
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
     const int s = it % NST;
@@ -235,22 +260,22 @@ __device__ void producer(Smem& sm, const TcLat* __restrict__ lats, int nlat, int
     const TileRef tr = tile_ref(L, t - L.tile_begin);
     const Geom& g = L.g;
     const int Vh = g.Vh;
-    // ---- phase A: neighbour table, links (threads 0..63), stored clover (64..127)
+    const int4 nb0 = pn0, nb1 = pn1;
+    fetch(t + gridDim.x);
+    // ---- links (threads 0..63) and stored clover (64..127) of the tile: loads first
     RawLink<R> lq;
     int lhop = 0, lsite = -1;
     uint4 cq = make_uint4(0, 0, 0, 0), cq8 = make_uint4(0, 0, 0, 0);
     int cq_site = -1, cq_c = 0;
     if (tid < TS * 8) {
-      const int i = tid & (TS - 1), hop = tid / TS;
+      const int hop = tid / TS;
       const int mu = hop >> 1, dir = hop & 1;
-      const int cb = tr.cb0 + i;
+      const int cb = tr.cb0 + my_i;
       if (cb < Vh) {
-        const int nb = __ldg(L.nbr + ((size_t)(tr.par * 8 + hop) * Vh + cb));
-        S.nbr[i][hop] = nb;
-        const int ycb = nb & 0x7fffffff;
+        const int ycb = nbr_of(nb0, nb1, hop) & 0x7fffffff;
         load_raw_link<R>(L.gauge, Vh, mu, dir == 0 ? tr.par : 1 - tr.par, dir == 0 ? cb : ycb, lq);
         lhop = hop;
-        lsite = i;
+        lsite = my_i;
       }
     } else {
       // 64 threads, 8 per site: stored clover chunk c (thread c = 0 also chunk 8)
@@ -267,9 +292,7 @@ __device__ void producer(Smem& sm, const TcLat* __restrict__ lats, int nlat, int
         cq_c = c;
       }
     }
-    bar_sync(BAR_PROD, NPT);
-    // ---- phase B: gather items (site i, rhs r, hop half hh) issue their loads
-    // the link and clover chunks loaded in phase A are stored now
+    // the link and clover chunks are stored once they arrive
     if (lsite >= 0) store_link<R>(lq, lhop & 1, reinterpret_cast<uint4*>(&S.link[lsite][lhop * 12]));
     if (cq_site >= 0) {
       uint4* dst = reinterpret_cast<uint4*>(&S.craw[cq_site][0]);
@@ -300,9 +323,7 @@ __device__ void producer(Smem& sm, const TcLat* __restrict__ lats, int nlat, int
       const char* fld = L.in + (size_t)(tr.rg * ROWS + rloc) * L.field_bytes;
       const char* src = fld + (size_t)(1 - tr.par) * hb;   // neighbours: other parity
       const char* self = fld + (size_t)tr.par * hb;
-      const int4 nb0 = *reinterpret_cast<const int4*>(&S.nbr[i][0]);
-      const int4 nb1 = *reinterpret_cast<const int4*>(&S.nbr[i][4]);
-      const int nb[8] = {nb0.x, nb0.y, nb0.z, nb0.w, nb1.x, nb1.y, nb1.z, nb1.w};
+      const int nb[8] = {nb0.x, nb0.y, nb0.z, nb0.w, nb1.x, nb1.y, nb1.z, nb1.w};  // site i == my_i
       const int4 nbs = hh ? nb1 : nb0;  // this half's 4 hops
       const int nh[4] = {nbs.x, nbs.y, nbs.z, nbs.w};
       // loads first: all 8 norms, own norm, this half's 4 neighbour spinors
@@ -582,7 +603,7 @@ namespace tc {
 __global__ void nbr_kernel(const Geom g, int* table) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= 2 * 8 * g.Vh) return;
-  const int cb = k % g.Vh, ph = k / g.Vh, hop = ph & 7, par = ph >> 3;
+  const int hop = k & 7, pc = k >> 3, cb = pc % g.Vh, par = pc / g.Vh;
   const int mu = hop >> 1, dir = hop & 1;
   int x[4];
   cb_coords(g, cb, par, x);

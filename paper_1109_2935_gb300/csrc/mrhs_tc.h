@@ -22,7 +22,7 @@ struct TcLat {
   int ctiles;      // tiles of sites per parity
   int tiles;       // ctiles * 2 parities * right-hand-side groups of 16
   int tile_begin;  // first tile of this lattice in the batch
-  const int* nbr;  // [parity][hop][Vh]: neighbour cb of each hop (hop = 2 mu + dir, dir 0
+  const int* nbr;  // [parity][Vh][hop]: neighbour cb of each hop (hop = 2 mu + dir, dir 0
                    // forward), bit 31 set when the hop crosses the antiperiodic t edge
 };
 
