@@ -687,8 +687,9 @@ int solve_gcr(Ctx& S, char* x, const char* b, const dirac_solver_params& P, int 
   // Each preconditioner has its own captured steps. With K_SELECT (not forced) the choice
   // is revisited at every restart: the residual reduction per second of the cycle just
   // finished (natural log of ||r|| per second of wall time) is kept per preconditioner;
-  // the other one is tried once, and afterwards whichever has the higher last measured
-  // rate runs the next cycle (flexible GCR admits a change of K at a restart).
+  // the other one is tried once (if its one-step test reduced the residual at all), and
+  // afterwards whichever has the higher last measured rate runs the next cycle (flexible
+  // GCR admits a change of K at a restart).
   StepGraphs cap_n(kmax, S.graphs), cap_s(kmax, S.graphs), cap_p(kmax, S.graphs);
   StepGraphs* caps[3] = {&cap_n, &cap_s, &cap_p};
   const bool adaptive = precond == K_SELECT && !S.c->ptc_force;
@@ -732,7 +733,11 @@ int solve_gcr(Ctx& S, char* x, const char* b, const dirac_solver_params& P, int 
         const double secs = std::chrono::duration<double>(now - cycle_t0).count();
         if (secs > 0 && r0n2 > 0 && cycle_r0 > 0) rate[kind] = 0.5 * std::log(cycle_r0 / r0n2) / secs;
         const int other = kind == K_SCHWARZ ? K_PTC : K_SCHWARZ;
-        if (rate[other] < 0 || rate[other] > rate[kind]) {
+        // a preconditioner whose one-step test reduced nothing (||r0 - M K r0|| >= ||r0||,
+        // e.g. an untrained network with K = 0) is never tried: its GCR step would break down
+        const double red_other = S.stats->precond_reduction[other - 1];
+        const bool usable = finite(red_other) && red_other < 1.0;
+        if (usable && (rate[other] < 0 || rate[other] > rate[kind])) {
           kind = other;
           S.stats->precond_switches++;
         }
