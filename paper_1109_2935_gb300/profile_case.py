@@ -5,6 +5,7 @@ profiler to capture (``ncu -k <kernel> ...``) and for a quick CUDA-event timing.
     python -m paper_1109_2935_gb300.profile_case batch --dims 24 24 24 64 --nrhs 12 --kernel cc
     python -m paper_1109_2935_gb300.profile_case ptc --dims 16 16 16 16 --channels 1 2 2 1
     python -m paper_1109_2935_gb300.profile_case wilson --dims 24 24 24 64 --prec f16
+    python -m paper_1109_2935_gb300.profile_case schwarz --dims 24 24 24 128 --prec f16
 
 Each case does `--warmup` untimed applications and `--steps` timed ones and prints one
 JSON line (milliseconds per application and algorithmic GB/s of the operator). Every
@@ -19,11 +20,16 @@ Cases:
           (FP32 fields; `--tensor-cores 0` for the FP32 layers).
   wilson  the full operator M on one right-hand side in the given storage precision
           (algorithmic bytes per site: FP64-18 1536, FP32-12 672, FP16-12 344).
+  schwarz the Schwarz preconditioner K (4^4 blocks, 6 minimal-residual steps) in the given
+          storage precision; flops per site: 6 x (1872 for M_B + 192 for the MR update and
+          the three block reductions).
 """
 import argparse
 import json
 
 SITE_BYTES = {"f64": 1536, "f32": 672, "f16": 344}
+# 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz
+FP32_PEAK_TFLOPS = 80.5
 
 
 def _event_ms(fn, steps, warmup):
@@ -98,9 +104,25 @@ def case_wilson(args, dirac, synth):
             "alg_GBps": round(alg / ms / 1e6, 1)}
 
 
+def case_schwarz(args, dirac, synth):
+    dims = tuple(args.dims)
+    pid = {"f64": dirac.F64, "f32": dirac.F32, "f16": dirac.F16}[args.prec]
+    U = synth.wilson_gauge(dims, 0.5, 3, 4003, device="cuda")
+    lat = dirac.Lattice(dims, dirac.WILSON_CLOVER, kappa=0.124, csw=1.0, block=(4, 4, 4, 4), mr_steps=6,
+                        recon=(18, 12, 12), prec_mask=(1 << dirac.F64) | (1 << pid))
+    lat.load_gauge(U)
+    x = lat.to_device(synth.wilson_spinor(dims, 4004, device="cuda"), pid)
+    y = lat.new_field(pid)
+    ms = _event_ms(lambda: lat.schwarz(y, x, pid), args.steps, args.warmup)
+    flops = lat.volume * 6 * (1872 + 192)
+    lat.close()
+    return {"case": "schwarz", "prec": args.prec, "dims": dims, "ms": round(ms, 4),
+            "tflops": round(flops / ms / 1e9, 2), "frac_of_fp32_peak": round(flops / ms / 1e9 / FP32_PEAK_TFLOPS, 4)}
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
-    ap.add_argument("case", choices=["batch", "ptc", "wilson"])
+    ap.add_argument("case", choices=["batch", "ptc", "wilson", "schwarz"])
     ap.add_argument("--dims", type=int, nargs=4, default=[24, 24, 24, 64])
     ap.add_argument("--nrhs", type=int, default=12)
     ap.add_argument("--kernel", choices=["cc", "tc"], default="tc")
@@ -111,7 +133,7 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     args = ap.parse_args(argv)
     from paper_1109_2935_gb300 import dirac, synth
-    fn = {"batch": case_batch, "ptc": case_ptc, "wilson": case_wilson}[args.case]
+    fn = {"batch": case_batch, "ptc": case_ptc, "wilson": case_wilson, "schwarz": case_schwarz}[args.case]
     print(json.dumps(fn(args, dirac, synth)))
 
 

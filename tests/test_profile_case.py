@@ -9,7 +9,7 @@ def test_help_and_case_names(capsys):
         profile_case.main(["--help"])
     assert e.value.code == 0
     text = capsys.readouterr().out
-    for case in ("batch", "ptc", "wilson"):
+    for case in ("batch", "ptc", "wilson", "schwarz"):
         assert case in text
 
 
