@@ -10,9 +10,8 @@
 // keeps that extent's periodic / antiperiodic wrap.
 //
 // FP32/FP16 storage: the block's forward links and clover are copied into shared
-// memory (FP16 links with 12 or 8 stored reals are decoded once into FP32 rows 0-1;
-// the clover stays binary16, so an FP16 block needs 109 KB and two CTAs fit on an SM)
-// and decoded on use; the clover's FP16
+// memory in their storage format (raw chunks: binary16 stays binary16, so an FP16
+// block needs 87 KB and two CTAs fit on an SM) and decoded on use; the clover's FP16
 // per-site norm scales the 6-component input instead of the 36 entries. The hopping
 // sum is accumulated unscaled and multiplied by -kappa once, only a wrapping t hop
 // with antiperiodic time taking its sign. The residual r lives in shared memory in
@@ -41,14 +40,7 @@ template <int PREC, int R>
 struct SchwarzLayout {
   using T = typename Real<PREC>::T;
   static constexpr bool kStage = PREC != P64;
-  // format of the staged links: FP16 links with 12 or 8 stored reals are decoded once
-  // into FP32 rows 0 and 1 (row 2 rebuilt per hop), so the 6 x 8 hops of the MR steps
-  // convert nothing; 192 B per site keeps two 256-site CTAs per SM
-  static constexpr bool kWiden = PREC == P16 && R != 18;
-  static constexpr int kLinkPrec = kWiden ? P32 : PREC;
-  static constexpr int kLinkR = kWiden ? 12 : R;
-  using SLIO = LinkIO<kLinkPrec, kLinkR>;
-  static constexpr int kLinkSite = kStage ? 4 * SLIO::kChunks * SLIO::kChunkBytes : 0;
+  static constexpr int kLinkSite = kStage ? 4 * LinkIO<PREC, R>::kChunks * LinkIO<PREC, R>::kChunkBytes : 0;
   static constexpr int kClovSite = kStage ? (PREC == P32 ? 288 : 148) : 0;
   static constexpr int kRSite = 24 * (int)sizeof(T);
   static constexpr int kSite = kRSite + kLinkSite + kClovSite;  // bytes of smem per block site
@@ -219,22 +211,7 @@ __global__ void __launch_bounds__(kMaxBlockSites, (SchwarzLayout<PREC, R>::kMinB
     SpinorIO<RP, 24>::store(r_s, nbs, t, v);
 #pragma unroll
     for (int k = 0; k < 24; ++k) xs[k] = 0;
-    if constexpr (L::kWiden) {
-      constexpr int SCH = L::SLIO::kChunks;  // 3 float4 chunks: rows 0 and 1
-#pragma unroll
-      for (int mu = 0; mu < 4; ++mu) {
-        Link<float> U;
-        LIO::load(a.gauge, Vh, mu, par, cb, U);
-        char* sp = l_s + (size_t)mu * SCH * 16 * nbs;
-#pragma unroll
-        for (int k = 0; k < SCH; ++k) {
-          const int e = 2 * k;  // complex entries 2k, 2k + 1 of rows 0-1 (row-major)
-          *reinterpret_cast<float4*>(sp + ((size_t)k * nbs + t) * 16) =
-              make_float4(U.m[e / 3][e % 3].r, U.m[e / 3][e % 3].i, U.m[(e + 1) / 3][(e + 1) % 3].r,
-                          U.m[(e + 1) / 3][(e + 1) % 3].i);
-        }
-      }
-    } else if constexpr (L::kStage) {
+    if constexpr (L::kStage) {
       constexpr int CB = LIO::kChunkBytes, NCH = LIO::kChunks;
 #pragma unroll
       for (int mu = 0; mu < 4; ++mu) {
@@ -244,8 +221,6 @@ __global__ void __launch_bounds__(kMaxBlockSites, (SchwarzLayout<PREC, R>::kMinB
         for (int k = 0; k < NCH; ++k)
           copy_chunk<CB>(sp + ((size_t)k * nbs + t) * CB, gp + ((size_t)k * Vh + cb) * CB);
       }
-    }
-    if constexpr (L::kStage) {
       constexpr int CCH = PREC == P32 ? 18 : 9;
 #pragma unroll
       for (int k = 0; k < CCH; ++k)
@@ -279,8 +254,7 @@ __global__ void __launch_bounds__(kMaxBlockSites, (SchwarzLayout<PREC, R>::kMinB
           Link<T> U;
           const int ls = dir == 0 ? t : lt;  // forward: own link; backward: the neighbour's
           if constexpr (L::kStage) {
-            using SL = typename L::SLIO;
-            SL::template load_plane<false>(l_s + (size_t)mu * SL::kChunks * SL::kChunkBytes * nbs, nbs, ls, U);
+            LIO::template load_plane<false>(l_s + (size_t)mu * LIO::kChunks * LIO::kChunkBytes * nbs, nbs, ls, U);
           } else {
             if (dir == 0) {
               LIO::load(a.gauge, Vh, mu, par, cb, U);
