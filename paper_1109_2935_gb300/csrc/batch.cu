@@ -38,6 +38,9 @@ struct BatchLat {
   int tiles_site;       // 32-site groups over the 2 Vh output sites
   int tiles;            // tiles_site * ceil(nrhs / RG)
   int tile_begin;       // first tile of this lattice in the batch
+  int rhs0;             // plan-wide index of this lattice's first right-hand side
+  const double* mask;   // null, or mask[(rhs0 + r) * mstride] == 0: right-hand side r is skipped
+  int mstride;
 };
 
 template <int PREC, int R>
@@ -46,6 +49,7 @@ __device__ __forceinline__ void batch_tile(const BatchLat& L, int t, int RG) {
   const int rg = t / rgroups_site, sg = t - rg * rgroups_site;
   const int rhs = rg * RG + threadIdx.y;
   if (rhs >= L.nrhs) return;
+  if (L.mask && L.mask[(size_t)(L.rhs0 + rhs) * L.mstride] == 0.0) return;
   WilsonArg a;
   a.g = L.g;
   a.gauge = L.gauge;
@@ -122,6 +126,9 @@ static BatchLat describe(const dirac_ctx* c, int prec, const void* in, void* out
   L.tiles_site = (int)((2 * c->Vh + kTileSites - 1) / kTileSites);
   L.tiles = L.tiles_site * ((nrhs + RG - 1) / RG);
   L.tile_begin = 0;
+  L.rhs0 = 0;
+  L.mask = nullptr;
+  L.mstride = 0;
   return L;
 }
 
@@ -259,9 +266,11 @@ int batch_create(dirac_ctx* const* ctxs, int nlat, void* const* out, const void*
   b->prec = prec;
   b->recon = recon;
   b->ds = ds;
-  for (int l = 0; l < nlat; ++l) {
+  for (int l = 0, r0 = 0; l < nlat; ++l) {
     b->ctxs.push_back(ctxs[l]);
     b->lats.push_back(describe(ctxs[l], prec, in[l], out[l], nrhs[l], 1));
+    b->lats.back().rhs0 = r0;
+    r0 += nrhs[l];
   }
   if (cudaMalloc(&b->d_lats, sizeof(BatchLat) * nlat) != cudaSuccess) {
     cudaGetLastError();
@@ -393,6 +402,25 @@ int batch_create(dirac_ctx* const* ctxs, int nlat, void* const* out, const void*
   }
   *plan = b;
   return cudaStreamSynchronize(st) == cudaSuccess ? DIRAC_OK : DIRAC_ERR_CUDA;
+}
+
+// Right-hand sides whose mask entry is 0 are skipped by the CUDA-core kernels (their
+// outputs are left as they are); a masked plan uses the CUDA-core kernel. The mask is
+// read at every launch, so it may change between launches and inside captured graphs.
+int batch_set_mask(dirac_batch* b, const double* mask, int stride, cudaStream_t st) {
+  if (!b) return DIRAC_ERR_ARG;
+  for (BatchLat& L : b->lats) {
+    L.mask = mask;
+    L.mstride = stride;
+  }
+  if (mask && b->use_tc) {
+    b->use_tc = false;
+    b->tuned_ms = b->cc_ms;
+  }
+  if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
+  if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
+  b->graph_napply = 0;
+  return batch_layout(b, b->RG, st);
 }
 
 }  // namespace dirac

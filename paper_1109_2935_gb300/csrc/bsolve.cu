@@ -11,9 +11,10 @@
 // GPU; every iteration is replayed from a CUDA graph (two graphs: the iteration's
 // launches depend only on the mirror slot). The host reads the per-right-hand-side
 // residual norms one iteration behind from mapped memory and decides reliable updates
-// (taken for all right-hand sides together when any of them asks) and convergence; a
-// converged right-hand side is frozen (its coefficients are zero, so x, the correction
-// and the residual stay as they are) while the others continue.
+// (taken together, in one set of launches, for the right-hand sides that ask; the others
+// are masked out and keep iterating) and convergence; a converged right-hand side is
+// frozen (masked out of the operator and BLAS launches, so x, the correction and the
+// residual stay as they are) while the others continue.
 #include <chrono>
 #include <cmath>
 #include <string>
@@ -285,15 +286,18 @@ __device__ __forceinline__ void block_sum(double v[3], int n) {
 // right-hand side, block within it). Reductions: per right-hand side, each block writes
 // its partial sums; the last block of that right-hand side adds them in block order
 // (deterministic) into its scalar slots.
+// A right-hand side whose mask entry (mask[rhs * mstride], when mask is given) is 0 is
+// skipped by all its blocks: no site work, no partial sums, its ticket untouched.
 template <class Op>
 __global__ void __launch_bounds__(NT) mb_kernel(const Seg* __restrict__ segs, int nseg, Op op, double* scal,
-                                                double* part, unsigned* tick) {
+                                                double* part, unsigned* tick, const double* mask, int mstride) {
   int l = 0;
   while (l + 1 < nseg && (int)blockIdx.x >= segs[l + 1].blk0) ++l;
   const Seg& g = segs[l];
   const int k = blockIdx.x - g.blk0;
   const int r = k / g.bpr, bx = k - r * g.bpr;
   const int rhs = g.rhs0 + r;
+  if (mask && mask[(size_t)rhs * mstride] == 0.0) return;  // uniform over the block
   double* sc = scal + (size_t)rhs * NSC;
   double acc[3] = {0, 0, 0};
   const int n = 2 * g.Vh;
@@ -402,10 +406,11 @@ __global__ void k_b4(double* scal, int n, double* mirror) {
   mirror[2 * j] = S[SC_RN];
   mirror[2 * j + 1] = S[SC_FLAG];
 }
-// start / after a reliable update: rho = (r0, rs) (in SC_TMP); active flags from the host
-__global__ void k_restart(double* scal, int n, const double* active, int first) {
+// start / after a reliable update of the right-hand sides with upd[j] != 0: rho = (r0, rs)
+// (in SC_TMP); active flags from the host
+__global__ void k_restart(double* scal, int n, const double* active, const double* upd, int first) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= n) return;
+  if (j >= n || upd[j] == 0.0) return;
   double* S = scal + (size_t)j * NSC;
   if (first) {
     S[SC_RHOOLD] = 1; S[SC_RHOOLD + 1] = 0;
@@ -438,7 +443,8 @@ struct Run {
   double* scal = nullptr;
   double* part = nullptr;
   unsigned* tick = nullptr;
-  double* host = nullptr;      // mapped: [2][nrhs][2] mirror, then [nrhs] gathered values, [nrhs] active
+  double* host = nullptr;      // mapped: [2][nrhs][2] mirror, [nrhs] gathered values, [nrhs] active,
+                               // [nrhs] reliable-update mask
   double* dhost = nullptr;
   std::vector<void*> bufs;
   dirac_batch* plan_pv = nullptr;
@@ -470,11 +476,18 @@ struct Run {
   volatile double* hgathered() { return host + 4 * nrhs; }
   double* active_d() { return dhost + 5 * nrhs; }
   double* active_h() { return host + 5 * nrhs; }
+  double* upd_d() { return dhost + 6 * nrhs; }
+  double* upd_h() { return host + 6 * nrhs; }
 };
 
+// which right-hand sides a batched BLAS launch covers
+enum : int { ALL = 0, ACTIVE = 1, UPDATING = 2 };
+
 template <class Op>
-int launch(Run& R, const Op& op) {
-  mb_kernel<Op><<<R.nblk, NT, 0, R.st>>>(R.d_segs, R.nseg, op, R.scal, R.part, R.tick);
+int launch(Run& R, const Op& op, int which = ALL) {
+  const double* mask = which == ACTIVE ? R.scal + SC_ACTIVE : (which == UPDATING ? R.upd_d() : nullptr);
+  const int stride = which == ACTIVE ? NSC : 1;
+  mb_kernel<Op><<<R.nblk, NT, 0, R.st>>>(R.d_segs, R.nseg, op, R.scal, R.part, R.tick, mask, stride);
   return cudaGetLastError() == cudaSuccess ? DIRAC_OK : DIRAC_ERR_CUDA;
 }
 int scalar(Run& R, int which, int slot = 0) {
@@ -497,25 +510,27 @@ int scalar(Run& R, int which, int slot = 0) {
 // one BiCGstab iteration of every right-hand side (launches depend only on `slot`)
 template <int SP, int AP>
 int iteration(Run& R, int slot) {
+  // right-hand sides that are not active (converged or failed) are skipped throughout
   RT(scalar(R, 1));
-  RT(launch(R, OpPUpd<SP>{}));
+  RT(launch(R, OpPUpd<SP>{}, ACTIVE));
   RT(dirac_batch_apply(R.plan_pv, R.st));  // v = M p
-  RT(launch(R, OpCdot<SP, VR0, VV, SC_SIGMA>{}));
+  RT(launch(R, OpCdot<SP, VR0, VV, SC_SIGMA>{}, ACTIVE));
   RT(scalar(R, 2));
-  RT(launch(R, OpSUpd<SP>{}));             // s = r - alpha v
+  RT(launch(R, OpSUpd<SP>{}, ACTIVE));     // s = r - alpha v
   RT(dirac_batch_apply(R.plan_st, R.st));  // t = M s
-  RT(launch(R, OpTS<SP>{}));
+  RT(launch(R, OpTS<SP>{}, ACTIVE));
   RT(scalar(R, 3));
-  RT(launch(R, OpXR<SP, AP>{}));
+  RT(launch(R, OpXR<SP, AP>{}, ACTIVE));
   RT(scalar(R, 4, slot));
   return DIRAC_OK;
 }
 
 // r = b - M x (FP64 fields) with the given plan; the per-rhs ||r||^2 is left in the host
 // array gathered()
+// (the right-hand sides with upd[j] != 0 only)
 int residual(Run& R, dirac_batch* plan) {
   RT(dirac_batch_apply(plan, R.st));   // r = M x
-  RT(launch(R, OpXmy{}));
+  RT(launch(R, OpXmy{}, UPDATING));
   k_gather<<<(R.nrhs + 63) / 64, 64, 0, R.st>>>(R.scal, R.nrhs, SC_RR, R.gathered());
   if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(R.st) != cudaSuccess) return DIRAC_ERR_CUDA;
   return DIRAC_OK;
@@ -524,15 +539,15 @@ int residual(Run& R, dirac_batch* plan) {
 // double-single arithmetic when the plan for it exists (exact = false) else in FP64
 template <int SP, int AP>
 int reliable(Run& R, bool exact) {
-  RT(launch(R, OpXUpd<AP>{}));
+  RT(launch(R, OpXUpd<AP>{}, UPDATING));
   return residual(R, (exact || !R.plan_xds) ? R.plan_x : R.plan_xds);
 }
 template <int SP, int AP>
 int restart(Run& R, int first) {
-  RT(launch(R, OpRestart<SP, AP>{}));
-  RT(launch(R, OpCdot<SP, VR0, VRS, SC_TMP>{}));
+  RT(launch(R, OpRestart<SP, AP>{}, UPDATING));
+  RT(launch(R, OpCdot<SP, VR0, VRS, SC_TMP>{}, UPDATING));
   // the host's active flags (pinned, mapped) for the scalar state
-  k_restart<<<(R.nrhs + 63) / 64, 64, 0, R.st>>>(R.scal, R.nrhs, R.active_d(), first);
+  k_restart<<<(R.nrhs + 63) / 64, 64, 0, R.st>>>(R.scal, R.nrhs, R.active_d(), R.upd_d(), first);
   return cudaGetLastError() == cudaSuccess ? DIRAC_OK : DIRAC_ERR_CUDA;
 }
 
@@ -547,6 +562,7 @@ int solve_batched_impl(Run& R, const dirac_solver_params& P, dirac_solver_stats*
   if (cudaStreamSynchronize(R.st) != cudaSuccess) return DIRAC_ERR_CUDA;
   std::vector<double> target(n), rmax(n), rr(n);
   std::vector<int> active(n, 1), relup(n, 0);
+  for (int j = 0; j < n; ++j) R.upd_h()[j] = 1;  // the start covers every right-hand side
   for (int j = 0; j < n; ++j) {
     bb[j] = R.hgathered()[j];
     if (!std::isfinite(bb[j])) {
@@ -623,6 +639,7 @@ int solve_batched_impl(Run& R, const dirac_solver_params& P, dirac_solver_stats*
       volatile double* m = R.hmirror(ps);
       bool upd = false;
       for (int j = 0; j < n; ++j) {
+        R.upd_h()[j] = 0;
         if (!active[j]) continue;
         const int fl = (int)m[2 * j + 1];
         if (fl != FL_OK) {
@@ -631,7 +648,10 @@ int solve_batched_impl(Run& R, const dirac_solver_params& P, dirac_solver_stats*
           continue;
         }
         const double rp = m[2 * j];
-        if ((d2 > 0 && rp < d2 * rmax[j]) || rp < target[j]) upd = true;
+        if ((d2 > 0 && rp < d2 * rmax[j]) || rp < target[j]) {
+          upd = true;
+          R.upd_h()[j] = 1;  // only the right-hand sides that ask are updated
+        }
       }
       if (upd) {
         nvtxRangePushA("batched reliable update (FP64)");
@@ -640,14 +660,12 @@ int solve_batched_impl(Run& R, const dirac_solver_params& P, dirac_solver_stats*
         // by the FP64 operator
         bool fresh = false;
         for (int j = 0; rc == DIRAC_OK && j < n; ++j)
-          fresh = fresh || (active[j] && R.hgathered()[j] < target[j]);
+          fresh = fresh || (R.upd_h()[j] != 0 && R.hgathered()[j] < target[j]);
         if (rc == DIRAC_OK && fresh && R.plan_xds) rc = residual(R, R.plan_x);
         if (rc == DIRAC_OK) {
           for (int j = 0; j < n; ++j) {
-            if (!active[j]) {
-              R.active_h()[j] = 0;
-              continue;
-            }
+            R.active_h()[j] = active[j];
+            if (R.upd_h()[j] == 0) continue;
             rr[j] = R.hgathered()[j];
             relup[j]++;
             if (rr[j] < target[j]) active[j] = 0;
@@ -664,7 +682,13 @@ int solve_batched_impl(Run& R, const dirac_solver_params& P, dirac_solver_stats*
   }
   if (rc == DIRAC_OK) {
     // fold in what is left of the sloppy corrections and take the final FP64 residuals
-    rc = reliable<SP, AP>(R, true);
+    // of every right-hand side
+    if (cudaStreamSynchronize(R.st) != cudaSuccess) {
+      rc = DIRAC_ERR_CUDA;
+    } else {
+      for (int j = 0; j < n; ++j) R.upd_h()[j] = 1;
+      rc = reliable<SP, AP>(R, true);
+    }
     if (rc == DIRAC_OK)
       for (int j = 0; j < n; ++j) rr[j] = R.hgathered()[j];
   }
@@ -755,12 +779,12 @@ extern "C" int solve_batched(dirac_ctx* const* ctxs, int nlat, void* const* x, c
       cudaMalloc(&R.scal, sizeof(double) * NSC * tot) != cudaSuccess ||
       cudaMalloc(&R.part, sizeof(double) * 3 * MAXBPR * tot) != cudaSuccess ||
       cudaMalloc(&R.tick, sizeof(unsigned) * tot) != cudaSuccess ||
-      cudaHostAlloc(&R.host, sizeof(double) * 6 * tot, cudaHostAllocMapped) != cudaSuccess ||
+      cudaHostAlloc(&R.host, sizeof(double) * 7 * tot, cudaHostAllocMapped) != cudaSuccess ||
       cudaHostGetDevicePointer(&R.dhost, R.host, 0) != cudaSuccess) {
     cudaGetLastError();
     return set_err(ctxs[0], DIRAC_ERR_OOM, "solve_batched: scalar state");
   }
-  for (int j = 0; j < 6 * tot; ++j) R.host[j] = 0;
+  for (int j = 0; j < 7 * tot; ++j) R.host[j] = 0;
   cudaMemsetAsync(R.scal, 0, sizeof(double) * NSC * tot, R.st);
   cudaMemsetAsync(R.tick, 0, sizeof(unsigned) * tot, R.st);
   cudaMemcpyAsync(R.d_segs, R.segs.data(), sizeof(Seg) * nlat, cudaMemcpyHostToDevice, R.st);
@@ -786,6 +810,12 @@ extern "C" int solve_batched(dirac_ctx* const* ctxs, int nlat, void* const* x, c
     for (int l = 0; l < nlat; ++l) ds = ds && ctxs[l]->ds_residual && ds_available(ctxs[l]);
     if (!rc && ds)
       rc = batch_create(ctxs, nlat, rout.data(), (const void* const*)xin.data(), nrhs, P64, R.st, &R.plan_xds, 0, true);
+    // the sloppy plans skip right-hand sides that are no longer active, the FP64 plans
+    // those that are not being updated
+    if (!rc) rc = batch_set_mask(R.plan_pv, R.scal + SC_ACTIVE, NSC, R.st);
+    if (!rc) rc = batch_set_mask(R.plan_st, R.scal + SC_ACTIVE, NSC, R.st);
+    if (!rc) rc = batch_set_mask(R.plan_x, R.upd_d(), 1, R.st);
+    if (!rc && R.plan_xds) rc = batch_set_mask(R.plan_xds, R.upd_d(), 1, R.st);
     if (rc) return set_err(ctxs[0], rc, "solve_batched: operator plans");
   }
   std::vector<double> bb(tot, 0.0);

@@ -152,6 +152,7 @@ int schur_reconstruct(dirac_ctx* c, char* x, const char* b, int prec, cudaStream
 // (ds: FP64 fields, 18-real links, arithmetic in double-single as dirac_apply_ds)
 int batch_create(dirac_ctx* const* ctxs, int nlat, void* const* out, const void* const* in, const int* nrhs,
                  int prec, cudaStream_t stream, dirac_batch** plan, int tune, bool ds = false);
+int batch_set_mask(dirac_batch* b, const double* mask, int stride, cudaStream_t st);
 
 // ---------------------------------------------------------------- PTC network (ptc.cu)
 // out = K in on FP32 full fields; flops of one application; free a network
