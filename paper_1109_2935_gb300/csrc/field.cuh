@@ -252,13 +252,23 @@ template <int PREC, int R> struct LinkIO;
 
 __device__ __forceinline__ size_t link_plane_bytes(int R, int w, int Vh) { return (size_t)R * w * Vh; }
 
+// row 2 = conj(row 0 x row 1): c = a_p b_q - a_q b_p as two chains of three fused
+// multiply-adds after one product per real part
 template <typename T>
 __device__ __forceinline__ void reconstruct12(Link<T>& U) {
 #pragma unroll
   for (int j = 0; j < 3; ++j) {
-    int a = (j + 1) % 3, b = (j + 2) % 3;
-    C<T> c = U.m[0][a] * U.m[1][b] - U.m[0][b] * U.m[1][a];
-    U.m[2][j] = conj(c);
+    const int p = (j + 1) % 3, q = (j + 2) % 3;
+    const C<T> ap = U.m[0][p], aq = U.m[0][q], bp = U.m[1][p], bq = U.m[1][q];
+    T cr = ap.r * bq.r;
+    cr = fma(-ap.i, bq.i, cr);
+    cr = fma(-aq.r, bp.r, cr);
+    cr = fma(aq.i, bp.i, cr);
+    T ci = ap.r * bq.i;
+    ci = fma(ap.i, bq.r, ci);
+    ci = fma(-aq.r, bp.i, ci);
+    ci = fma(-aq.i, bp.r, ci);
+    U.m[2][j] = C<T>{cr, -ci};
   }
 }
 
@@ -443,6 +453,13 @@ template <> struct CloverIO<P32> {
 };
 template <> struct CloverIO<P16> {
   __host__ __device__ static constexpr size_t parity_bytes(int64_t Vh) { return (size_t)148 * Vh; }
+  // the 72 stored values without the per-site norm, which is returned
+  __device__ static float load_raw(const char* b, int Vh, int cb, float v[72]) {
+    const float n = __ldg(reinterpret_cast<const float*>(b + (size_t)144 * Vh) + cb);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) unpack_half8(ldg_chunk<int4>(b + ((size_t)k * Vh + cb) * 16), v + 8 * k);
+    return n;
+  }
   __device__ static void load(const char* b, int Vh, int cb, float v[72]) {
     float n = __ldg(reinterpret_cast<const float*>(b + (size_t)144 * Vh) + cb);
 #pragma unroll

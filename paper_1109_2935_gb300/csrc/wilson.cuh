@@ -70,8 +70,6 @@ __device__ __forceinline__ void wilson_hop(C<T> acc[4][3], const T* psi, const L
       h0[c] = u0 + s * l0;
       h1[c] = u1 + s * l1;
     }
-    h0[c] = bc * h0[c];
-    h1[c] = bc * h1[c];
   }
   C<T> v0[3], v1[3];
   if (link_dag) {
@@ -81,22 +79,25 @@ __device__ __forceinline__ void wilson_hop(C<T> acc[4][3], const T* psi, const L
     su3_mv(U, h0, v0);
     su3_mv(U, h1, v1);
   }
+  // the hop's factor bc multiplies the accumulation (one fused multiply-add per real);
+  // with bc = +-1 (FP32 / FP64 storage) this is exactly acc +- v
+  const T ks = s * bc;
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
-    acc[0][c] = acc[0][c] + v0[c];
-    acc[1][c] = acc[1][c] + v1[c];
+    acc[0][c] = C<T>{fma(bc, v0[c].r, acc[0][c].r), fma(bc, v0[c].i, acc[0][c].i)};
+    acc[1][c] = C<T>{fma(bc, v1[c].r, acc[1][c].r), fma(bc, v1[c].i, acc[1][c].i)};
     if (MU == 0) {        // B^dagger v = (-i v1, -i v0)
-      acc[2][c] = acc[2][c] - s * times_i(v1[c]);
-      acc[3][c] = acc[3][c] - s * times_i(v0[c]);
+      acc[2][c] = C<T>{fma(ks, v1[c].i, acc[2][c].r), fma(-ks, v1[c].r, acc[2][c].i)};
+      acc[3][c] = C<T>{fma(ks, v0[c].i, acc[3][c].r), fma(-ks, v0[c].r, acc[3][c].i)};
     } else if (MU == 1) { // B^dagger v = (v1, -v0)
-      acc[2][c] = acc[2][c] + s * v1[c];
-      acc[3][c] = acc[3][c] - s * v0[c];
+      acc[2][c] = C<T>{fma(ks, v1[c].r, acc[2][c].r), fma(ks, v1[c].i, acc[2][c].i)};
+      acc[3][c] = C<T>{fma(-ks, v0[c].r, acc[3][c].r), fma(-ks, v0[c].i, acc[3][c].i)};
     } else if (MU == 2) { // B^dagger v = (-i v0, i v1)
-      acc[2][c] = acc[2][c] - s * times_i(v0[c]);
-      acc[3][c] = acc[3][c] + s * times_i(v1[c]);
+      acc[2][c] = C<T>{fma(ks, v0[c].i, acc[2][c].r), fma(-ks, v0[c].r, acc[2][c].i)};
+      acc[3][c] = C<T>{fma(-ks, v1[c].i, acc[3][c].r), fma(ks, v1[c].r, acc[3][c].i)};
     } else {
-      acc[2][c] = acc[2][c] + s * v0[c];
-      acc[3][c] = acc[3][c] + s * v1[c];
+      acc[2][c] = C<T>{fma(ks, v0[c].r, acc[2][c].r), fma(ks, v0[c].i, acc[2][c].i)};
+      acc[3][c] = C<T>{fma(ks, v1[c].r, acc[3][c].r), fma(ks, v1[c].i, acc[3][c].i)};
     }
   }
 }
@@ -129,10 +130,15 @@ __device__ __forceinline__ void apply_clover_site(const char* b, int Vh, int cb,
       herm6_mv<T>(v, in + 6 * blk, out + 6 * blk);
     }
   } else {
+    // 16-bit clover: the stored values times the per-site norm, which scales the 12
+    // input components instead of the 72 entries
     float v[72];
-    CloverIO<P16>::load(b, Vh, cb, v);
-    herm6_mv<T>(v, in, out);
-    herm6_mv<T>(v + 36, in + 6, out + 6);
+    const float n = CloverIO<P16>::load_raw(b, Vh, cb, v);
+    C<T> x[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) x[k] = n * in[k];
+    herm6_mv<T>(v, x, out);
+    herm6_mv<T>(v + 36, x + 6, out + 6);
   }
 }
 
@@ -237,8 +243,8 @@ __device__ __forceinline__ void wilson_site(const WilsonArg& a, int idx) {
   T out[24];
   if (FULLM) {
     T self[24];
-    SpinorIO<PREC, 24>::load(self_in, Vh, cb, self);
     C<T> sv[12], av[12];
+    SpinorIO<PREC, 24>::load(self_in, Vh, cb, self);
 #pragma unroll
     for (int k = 0; k < 12; ++k) sv[k] = C<T>{self[2 * k], self[2 * k + 1]};
     if (a.clover) {
