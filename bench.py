@@ -548,8 +548,10 @@ def measure_wilson_rows(lat, dirac, fields, precs, stream, peak):
         pid = PREC_ID[name]
         x, y = fields[name]
         lat.apply(y, x, -1, pid, stream)
-        for P in (2, 4, 8):
-            if lat.dims[3] % (2 * P):
+        # t-slabs, and grids that cut every dimension (Sec. 6.1-6.3)
+        for P in (2, 4, 8, (2, 2, 2, 2), (2, 2, 2, 4)):
+            grid = P if isinstance(P, tuple) else (1, 1, 1, P)
+            if any(d % (2 * g) for d, g in zip(lat.dims, grid)):
                 continue
             dd = dirac.DomainDecomposition(lat, P, pid)
             dd.scatter(x, stream=stream)
@@ -558,7 +560,8 @@ def measure_wilson_rows(lat, dirac, fields, precs, stream, peak):
             dd.gather(g, stream=stream)
             torch.cuda.synchronize()
             gbs = SITE_BYTES[name] * V / (ms / 1e3) / 1e9
-            out["domain_decomposition"].setdefault(name, {})[f"ranks_{P}"] = {
+            key = f"ranks_{P}" if not isinstance(P, tuple) else "grid_" + "x".join(map(str, P))
+            out["domain_decomposition"].setdefault(name, {})[key] = {
                 "ms": round(ms, 4), "alg_GBps": round(gbs, 1), "frac_of_hbm": round(gbs / peak, 4),
                 "face_bytes": dd.info()["face_bytes"],
                 # FP16: the two kernels round the decode product differently (one FP16 ulp)

@@ -387,18 +387,26 @@ int dirac_ptc_attach(dirac_ctx* ctx, dirac_ptc* net, int force);
 int dirac_ptc_destroy(dirac_ptc* net);
 
 /* ------------------------------------------------------------------ domain decomposition
- * The paper's multi-GPU scheme (Sec. 6) for the Wilson-clover operator, emulated on one
- * GPU: the lattice is cut along t into nranks virtual ranks (LT / nranks even, >= 2),
- * each with its own local links, clover and spinors, a stream, send buffers and two
- * ghost zones. dirac_dd_apply packs each rank's boundary slices spin-projected (12 reals
- * per face site: FP64 in FP64, else FP32), copies them into the neighbours' ghost zones
- * (device-to-device copies ordered by events), and runs the interior slices (overlapping
- * the exchange) and the boundary slices as separate kernels. Backward-hop links of the
- * face are exchanged once, by dirac_dd_create. The result equals dirac_apply(FULL) of the
- * whole lattice bit for bit in FP64 and FP32 (FP16: to FP32 rounding before re-encoding). Fields: `in` / `out` of scatter / gather are full fields of
- * ctx in precision `prec`. All calls are asynchronous on stream except create / destroy
- * (which synchronise the device). */
+ * The paper's multi-GPU scheme (Sec. 6: partitioning in up to four dimensions, spin-
+ * projected face exchange, interior computation overlapping the communication) for the
+ * Wilson-clover operator, emulated on one GPU: the lattice is cut by a grid of
+ * grid[0] x grid[1] x grid[2] x grid[3] virtual ranks (every L_mu / grid_mu an even
+ * integer >= 2; at most 256 ranks), each with its own local links, clover and spinors, a
+ * stream, send buffers and, for every cut dimension, two ghost zones of one slice.
+ * dirac_dd_apply packs each rank's boundary slices spin-projected (12 reals per face site:
+ * FP64 in FP64, else FP32), copies them into the neighbours' ghost zones (device-to-device
+ * copies ordered by events), and runs the interior (overlapping the exchange) and the
+ * boundary sites as separate kernels. Backward-hop links of the faces are exchanged once,
+ * by the create call. The result equals dirac_apply(FULL) of the whole lattice bit for bit
+ * in FP64 and FP32 (FP16: to one binary16 unit per site after re-encoding). Fields: `in` /
+ * `out` of scatter / gather are full fields of ctx in precision `prec`. All calls are
+ * asynchronous on stream except create / destroy (which synchronise the device).
+ * Errors: DIRAC_ERR_ARG for a grid that does not divide the lattice as required,
+ * DIRAC_ERR_OOM when rank storage cannot be allocated. */
 typedef struct dirac_dd dirac_dd;
+/* grid: ranks per dimension (x, y, z, t); 1 leaves a dimension whole */
+int dirac_dd_create_grid(dirac_ctx* ctx, const int* grid, dirac_prec prec, dirac_dd** dd);
+/* nranks ranks along t: the grid (1, 1, 1, nranks) */
 int dirac_dd_create(dirac_ctx* ctx, int nranks, dirac_prec prec, dirac_dd** dd);
 /* global field -> every rank's local input */
 int dirac_dd_scatter(dirac_dd* dd, const void* in, void* stream);
@@ -406,7 +414,7 @@ int dirac_dd_scatter(dirac_dd* dd, const void* in, void* stream);
 int dirac_dd_apply(dirac_dd* dd, int dagger, void* stream);
 /* every rank's local output -> global field */
 int dirac_dd_gather(dirac_dd* dd, void* out, void* stream);
-/* local dims of a rank; bytes of one spinor face */
+/* local dims of a rank; bytes of the spinor faces one rank receives per application */
 int dirac_dd_info(const dirac_dd* dd, int* local_dims, long long* face_bytes);
 int dirac_dd_destroy(dirac_dd* dd);
 

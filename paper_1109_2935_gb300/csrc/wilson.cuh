@@ -47,10 +47,11 @@ __device__ __forceinline__ T load_hop_spinor(const char* src, int Vh, int cb, T 
   }
 }
 
+// The spin projection of one hop: h = psi_up + s B_mu psi_low (two spin components,
+// 3 colours each). Shared by the stencil and by the face packing of the domain
+// decomposition, so that a projected face equals the stencil's own projection bit for bit.
 template <int MU, typename T>
-__device__ __forceinline__ void wilson_hop(C<T> acc[4][3], const T* psi, const Link<T>& U,
-                                           bool link_dag, T s, T bc) {
-  C<T> h0[3], h1[3];
+__device__ __forceinline__ void wilson_project(const T* psi, T s, C<T> h0[3], C<T> h1[3]) {
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     C<T> u0 = {psi[2 * c], psi[2 * c + 1]};
@@ -71,6 +72,13 @@ __device__ __forceinline__ void wilson_hop(C<T> acc[4][3], const T* psi, const L
       h1[c] = u1 + s * l1;
     }
   }
+}
+
+template <int MU, typename T>
+__device__ __forceinline__ void wilson_hop(C<T> acc[4][3], const T* psi, const Link<T>& U,
+                                           bool link_dag, T s, T bc) {
+  C<T> h0[3], h1[3];
+  wilson_project<MU, T>(psi, s, h0, h1);
   C<T> v0[3], v1[3];
   if (link_dag) {
     su3_mv_dag(U, h0, v0);

@@ -123,6 +123,7 @@ _SIGS = {
     "dirac_ptc_test_stall": (_ci, [_vp, _ci, _cd]),
     "dirac_ptc_destroy": (_ci, [_vp]),
     "dirac_dd_create": (_ci, [_vp, _ci, _ci, ctypes.POINTER(_vp)]),
+    "dirac_dd_create_grid": (_ci, [_vp, ctypes.POINTER(_ci), _ci, ctypes.POINTER(_vp)]),
     "dirac_dd_scatter": (_ci, [_vp, _vp, _vp]),
     "dirac_dd_apply": (_ci, [_vp, _ci, _vp]),
     "dirac_dd_gather": (_ci, [_vp, _vp, _vp]),
@@ -519,13 +520,18 @@ class Ptc:
 
 
 class DomainDecomposition:
-    """dirac_dd_*: the Wilson-clover operator over nranks virtual ranks (t-slabs) with
-    ghost zones and face exchange, on one GPU."""
+    """dirac_dd_*: the Wilson-clover operator over virtual ranks with ghost zones and face
+    exchange, on one GPU. `ranks` is a number of t-slabs or a grid (gx, gy, gz, gt) of
+    ranks per dimension."""
 
-    def __init__(self, lattice, nranks, prec):
+    def __init__(self, lattice, ranks, prec):
         self.lat = lattice
         h = _vp()
-        lattice.check(dirac_dd_create(lattice.ctx, nranks, prec, ctypes.byref(h)), "dirac_dd_create")
+        if isinstance(ranks, (tuple, list)):
+            grid = (_ci * 4)(*[int(v) for v in ranks])
+            lattice.check(dirac_dd_create_grid(lattice.ctx, grid, prec, ctypes.byref(h)), "dirac_dd_create_grid")
+        else:
+            lattice.check(dirac_dd_create(lattice.ctx, int(ranks), prec, ctypes.byref(h)), "dirac_dd_create")
         self.dd = h
 
     def info(self):
