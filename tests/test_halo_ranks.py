@@ -105,3 +105,87 @@ def test_rank_halo_exchange_matches_whole_lattice_and_times_out(world):
         assert abs(n2 - n2_ref) < 1e-12 * n2_ref
     assert got[0][4] and got[0][5] == -8
     assert not any(g[4] for g in got[1:])
+
+
+def _grid_worker(rank, world, port, grid, q):
+    """Rank `rank` of a (g_x, g_y, g_z, g_t) grid: faces and gauge ghosts exchanged in every
+    cut dimension, the oracle operator on the block plus one ghost layer per cut side."""
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    from oracle import wilson
+    from oracle.gamma import GAMMA
+    from paper_1109_2935_gb300 import synth
+    from paper_1109_2935_gb300.halo import HaloExchange
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    U = synth.wilson_gauge(DIMS, 0.5, 1, 4001).numpy()
+    psi = synth.wilson_spinor(DIMS, 4002).numpy()
+    A = wilson.clover(U, 1.0)
+    ref = wilson.apply_M(U, A, KAPPA, psi)            # whole lattice, antiperiodic t
+    hx = HaloExchange(timeout_s=5.0, grid=grid)
+    co = hx.coords
+    ax = lambda mu: 3 - mu                             # arrays are [t, z, y, x, ...]
+    loc_len = [DIMS[mu] // grid[mu] for mu in range(4)]
+    blk = [slice(None)] * 4
+    for mu in range(4):
+        blk[ax(mu)] = slice(co[mu] * loc_len[mu], (co[mu] + 1) * loc_len[mu])
+    blk = tuple(blk)
+    loc, Uloc, Aloc = psi[blk], U[blk], A[blk]
+    cut = [mu for mu in range(4) if grid[mu] > 1]
+    ext_shape = [loc.shape[a] + (2 if (3 - a) in cut else 0) for a in range(4)]
+    inner = tuple(slice(1, -1) if (3 - a) in cut else slice(None) for a in range(4))
+    ext = np.zeros(tuple(ext_shape) + loc.shape[4:], dtype=complex)
+    Uext = np.zeros(tuple(ext_shape) + U.shape[4:], dtype=complex)
+    Uext[:] = np.eye(3)
+    Aext = np.zeros(tuple(ext_shape) + A.shape[4:], dtype=complex)
+    ext[inner], Uext[inner], Aext[inner] = loc, Uloc, Aloc
+
+    def project(sl, mu, s):   # the two upper spin components of (1 + s gamma_mu) psi
+        P = (np.eye(4) + s * GAMMA[mu])[:2]
+        return np.einsum("ab,...bc->...ac", P, sl)
+
+    for mu in cut:
+        a = ax(mu)
+        first, last = np.take(loc, 0, axis=a), np.take(loc, loc_len[mu] - 1, axis=a)
+        from_next, from_prev = hx.exchange(torch.from_numpy(project(first, mu, -1.0)),
+                                           torch.from_numpy(project(last, mu, +1.0)), mu=mu)
+        h_next, h_prev = from_next.numpy().copy(), from_prev.numpy().copy()
+        if mu == 3 and co[3] == grid[3] - 1:
+            h_next *= -1.0                             # the hop crosses the antiperiodic edge
+        if mu == 3 and co[3] == 0:
+            h_prev *= -1.0
+        ulast = np.take(Uloc, loc_len[mu] - 1, axis=a)[..., mu, :, :].copy()
+        _, links_prev = hx.exchange(torch.zeros(1, dtype=torch.complex128), torch.from_numpy(ulast), mu=mu)
+        for at, h in ((0, h_prev), (-1, h_next)):
+            idx = list(inner)
+            idx[a] = at
+            ext[tuple(idx) + (slice(0, 2),)] = h       # ghost spinor [h; 0]
+        idx = list(inner)
+        idx[a] = 0
+        Uext[tuple(idx) + (mu,)] = links_prev.numpy()
+    out = wilson.apply_M(Uext, Aext, KAPPA, ext, antiperiodic_t=3 not in cut)[inner]
+    err = float(np.max(np.abs(out - ref[blk])))
+    n2 = hx.allreduce(torch.tensor([float(np.vdot(out, out).real)], dtype=torch.float64)).item()
+    dist.barrier()
+    q.put((rank, err, n2, float(np.vdot(ref, ref).real)))
+
+
+@pytest.mark.parametrize("grid", [(1, 1, 2, 2), (2, 2, 1, 1), (2, 1, 1, 2)])
+def test_rank_grid_halo_exchange_matches_whole_lattice(grid):
+    """Four gloo ranks cutting two dimensions: faces projected for every cut direction and
+    the backward gauge ghosts travel to the right neighbours, the antiperiodic sign goes to
+    the ranks on the t edge, and every block equals the whole-lattice oracle."""
+    world = int(np.prod(grid))
+    port = _free_port()
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_grid_worker, args=(r, world, port, grid, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(180)
+        assert p.exitcode == 0
+    got = sorted(q.get(timeout=10) for _ in range(world))
+    for rank, err, n2, n2_ref in got:
+        assert err < 1e-13, (rank, err)
+        assert abs(n2 - n2_ref) < 1e-12 * n2_ref
