@@ -74,11 +74,11 @@ __device__ __forceinline__ void wilson_project(const T* psi, T s, C<T> h0[3], C<
   }
 }
 
+// The rest of a hop after the projection: v = U h (U^dagger h for a backward hop), then
+// acc += bc P-reconstruction of v.
 template <int MU, typename T>
-__device__ __forceinline__ void wilson_hop(C<T> acc[4][3], const T* psi, const Link<T>& U,
-                                           bool link_dag, T s, T bc) {
-  C<T> h0[3], h1[3];
-  wilson_project<MU, T>(psi, s, h0, h1);
+__device__ __forceinline__ void wilson_hop_proj(C<T> acc[4][3], const C<T> h0[3], const C<T> h1[3],
+                                                const Link<T>& U, bool link_dag, T s, T bc) {
   C<T> v0[3], v1[3];
   if (link_dag) {
     su3_mv_dag(U, h0, v0);
@@ -108,6 +108,14 @@ __device__ __forceinline__ void wilson_hop(C<T> acc[4][3], const T* psi, const L
       acc[3][c] = C<T>{fma(ks, v1[c].r, acc[3][c].r), fma(ks, v1[c].i, acc[3][c].i)};
     }
   }
+}
+
+template <int MU, typename T>
+__device__ __forceinline__ void wilson_hop(C<T> acc[4][3], const T* psi, const Link<T>& U,
+                                           bool link_dag, T s, T bc) {
+  C<T> h0[3], h1[3];
+  wilson_project<MU, T>(psi, s, h0, h1);
+  wilson_hop_proj<MU, T>(acc, h0, h1, U, link_dag, s, bc);
 }
 
 // out[12] = Ahat(x) in[12] for the clover of precision PREC (block by block to bound
@@ -148,6 +156,139 @@ __device__ __forceinline__ void apply_clover_site(const char* b, int Vh, int cb,
     herm6_mv<T>(v, x, out);
     herm6_mv<T>(v + 36, x + 6, out + 6);
   }
+}
+
+// ---------------------------------------------------------------- 16-bit Ahat x self
+// fma of one binary16 half of word a and one of word b into an FP32 accumulator: the two
+// binary16 factors enter the fused multiply-add exactly (their product is exact in FP32),
+// so this equals converting both and one FP32 fma, without the conversions.
+template <int HA, int HB>
+__device__ __forceinline__ float fma_hh(uint32_t a, uint32_t b, float c) {
+  float d;
+  asm("{\n\t.reg .b16 a0, a1, b0, b1;\n\t"
+      "mov.b32 {a0, a1}, %1;\n\t"
+      "mov.b32 {b0, b1}, %2;\n\t"
+      "fma.rn.f32.f16 %0, a%4, b%5, %3;\n\t}"
+      : "=f"(d) : "r"(a), "r"(b), "f"(c), "n"(HA), "n"(HB));
+  return d;
+}
+
+// y = A x for one chirality block with the stored binary16 values of both: blk = the
+// block's 18 half2 words (6 real diagonal entries in words 0..2, then L_ij, i > j, one
+// complex per word), x = 6 complex binary16 words (re low, im high).
+__device__ __forceinline__ void herm6_hh(const uint32_t blk[18], const uint32_t x[6], C<float> y[6]) {
+  uint32_t nx[6];  // (-re, -im)
+#pragma unroll
+  for (int i = 0; i < 6; ++i) nx[i] = x[i] ^ 0x80008000u;
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    const uint32_t d = blk[i >> 1];
+    if (i & 1) y[i] = C<float>{fma_hh<1, 0>(d, x[i], 0.f), fma_hh<1, 1>(d, x[i], 0.f)};
+    else y[i] = C<float>{fma_hh<0, 0>(d, x[i], 0.f), fma_hh<0, 1>(d, x[i], 0.f)};
+  }
+  int w = 3;
+#pragma unroll
+  for (int i = 1; i < 6; ++i) {
+#pragma unroll
+    for (int j = 0; j < i; ++j) {
+      const uint32_t l = blk[w++];
+      // y_i += L x_j
+      y[i].r = fma_hh<1, 1>(l, nx[j], fma_hh<0, 0>(l, x[j], y[i].r));
+      y[i].i = fma_hh<1, 0>(l, x[j], fma_hh<0, 1>(l, x[j], y[i].i));
+      // y_j += conj(L) x_i
+      y[j].r = fma_hh<1, 1>(l, x[i], fma_hh<0, 0>(l, x[i], y[j].r));
+      y[j].i = fma_hh<1, 0>(l, nx[i], fma_hh<0, 1>(l, x[i], y[j].i));
+    }
+  }
+}
+
+// av = Ahat self for 16-bit storage, from the stored binary16 values of the clover and of
+// the site's own spinor; their two per-site norms scale the 12 results once.
+__device__ __forceinline__ void clover_self_h(const char* clov, const char* self, int Vh, int cb, C<float> av[12]) {
+  const float nc = __ldg(reinterpret_cast<const float*>(clov + (size_t)144 * Vh) + cb);
+  const float ns = __ldg(reinterpret_cast<const float*>(self + (size_t)48 * Vh) + cb);
+  uint32_t x[12];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const int4 q = ldg_chunk<int4>(self + ((size_t)k * Vh + cb) * 16);
+    x[4 * k] = (uint32_t)q.x; x[4 * k + 1] = (uint32_t)q.y; x[4 * k + 2] = (uint32_t)q.z; x[4 * k + 3] = (uint32_t)q.w;
+  }
+  // block 0: words 0..17 (chunks 0..3 and half of chunk 4); block 1: words 18..35
+  uint32_t c[20];
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    const int4 q = ldg_chunk<int4>(clov + ((size_t)k * Vh + cb) * 16);
+    c[4 * k] = (uint32_t)q.x; c[4 * k + 1] = (uint32_t)q.y; c[4 * k + 2] = (uint32_t)q.z; c[4 * k + 3] = (uint32_t)q.w;
+  }
+  herm6_hh(c, x, av);
+  c[0] = c[18];
+  c[1] = c[19];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int4 q = ldg_chunk<int4>(clov + ((size_t)(5 + k) * Vh + cb) * 16);
+    c[2 + 4 * k] = (uint32_t)q.x; c[3 + 4 * k] = (uint32_t)q.y; c[4 + 4 * k] = (uint32_t)q.z; c[5 + 4 * k] = (uint32_t)q.w;
+  }
+  herm6_hh(c, x + 6, av + 6);
+  const float n = nc * ns;
+#pragma unroll
+  for (int k = 0; k < 12; ++k) av[k] = n * av[k];
+}
+
+// ---------------------------------------------------------------- 16-bit neighbours
+// A 16-bit neighbour spinor for a hop: the upper two spin components converted (u, 12
+// reals), the lower two kept as binary16 pairs (l, 6 words: spin 2 colours 0..2, spin 3
+// colours 0..2, re low / im high); returns bc times the site norm, the hop's factor.
+__device__ __forceinline__ float load_hop_h(const char* src, int Vh, int cb, float u[12], uint32_t l[6], float bc) {
+  const float n = __ldg(reinterpret_cast<const float*>(src + (size_t)48 * Vh) + cb);
+  uint32_t w[12];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const int4 q = ldg_chunk<int4>(src + ((size_t)k * Vh + cb) * 16);
+    w[4 * k] = (uint32_t)q.x; w[4 * k + 1] = (uint32_t)q.y; w[4 * k + 2] = (uint32_t)q.z; w[4 * k + 3] = (uint32_t)q.w;
+  }
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    const float2 f = __half22float2(*reinterpret_cast<const __half2*>(&w[k]));
+    u[2 * k] = f.x;
+    u[2 * k + 1] = f.y;
+    l[k] = w[6 + k];
+  }
+  return bc * n;
+}
+
+// The projection of wilson_project with binary16 lower components: each real is one
+// fma of (s or -s) times a binary16 value into the FP32 upper value (sw: s in the low
+// half, -s in the high half). s = +-1, so the result is round(u +- l), as in FP32.
+template <int MU>
+__device__ __forceinline__ void wilson_project_h(const float u[12], const uint32_t l[6], uint32_t sw,
+                                                 C<float> h0[3], C<float> h1[3]) {
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const float u0r = u[2 * c], u0i = u[2 * c + 1], u1r = u[6 + 2 * c], u1i = u[7 + 2 * c];
+    const uint32_t l0 = l[c], l1 = l[3 + c];
+    if (MU == 0) {        // h = u + s (i l1, i l0)
+      h0[c] = C<float>{fma_hh<1, 1>(sw, l1, u0r), fma_hh<0, 0>(sw, l1, u0i)};
+      h1[c] = C<float>{fma_hh<1, 1>(sw, l0, u1r), fma_hh<0, 0>(sw, l0, u1i)};
+    } else if (MU == 1) { // h = u + s (-l1, l0)
+      h0[c] = C<float>{fma_hh<1, 0>(sw, l1, u0r), fma_hh<1, 1>(sw, l1, u0i)};
+      h1[c] = C<float>{fma_hh<0, 0>(sw, l0, u1r), fma_hh<0, 1>(sw, l0, u1i)};
+    } else if (MU == 2) { // h = u + s (i l0, -i l1)
+      h0[c] = C<float>{fma_hh<1, 1>(sw, l0, u0r), fma_hh<0, 0>(sw, l0, u0i)};
+      h1[c] = C<float>{fma_hh<0, 1>(sw, l1, u1r), fma_hh<1, 0>(sw, l1, u1i)};
+    } else {              // h = u + s l
+      h0[c] = C<float>{fma_hh<0, 0>(sw, l0, u0r), fma_hh<0, 1>(sw, l0, u0i)};
+      h1[c] = C<float>{fma_hh<0, 0>(sw, l1, u1r), fma_hh<0, 1>(sw, l1, u1i)};
+    }
+  }
+}
+__device__ __forceinline__ uint32_t signs_h(float s) { return s > 0.f ? 0xBC003C00u : 0x3C00BC00u; }
+
+template <int MU>
+__device__ __forceinline__ void wilson_hop_h(C<float> acc[4][3], const float u[12], const uint32_t l[6],
+                                             const Link<float>& U, bool link_dag, float s, float bc) {
+  C<float> h0[3], h1[3];
+  wilson_project_h<MU>(u, l, signs_h(s), h0, h1);
+  wilson_hop_proj<MU, float>(acc, h0, h1, U, link_dag, s, bc);
 }
 
 // Launch shape per storage precision (threads per CTA, minimum resident CTAs per SM,
@@ -219,14 +360,26 @@ __device__ __forceinline__ void wilson_site(const WilsonArg& a, int idx) {
         y[mu] = 0;
         if (mu == 3 && g.apbc) bc = -1;
       }
-      T psi[24];
-      bc = load_hop_spinor<PREC, T>(src, Vh, cb_index(g, y), psi, bc);
-      Link<T> U;
-      LinkIO<PREC, R>::load(a.gauge, Vh, mu, par, cb, U);
-      if (mu == 0) wilson_hop<0>(acc, psi, U, false, sf, bc);
-      if (mu == 1) wilson_hop<1>(acc, psi, U, false, sf, bc);
-      if (mu == 2) wilson_hop<2>(acc, psi, U, false, sf, bc);
-      if (mu == 3) wilson_hop<3>(acc, psi, U, false, sf, bc);
+      if constexpr (PREC == P16) {
+        float u[12];
+        uint32_t l[6];
+        bc = load_hop_h(src, Vh, cb_index(g, y), u, l, bc);
+        Link<T> U;
+        LinkIO<PREC, R>::load(a.gauge, Vh, mu, par, cb, U);
+        if (mu == 0) wilson_hop_h<0>(acc, u, l, U, false, sf, bc);
+        if (mu == 1) wilson_hop_h<1>(acc, u, l, U, false, sf, bc);
+        if (mu == 2) wilson_hop_h<2>(acc, u, l, U, false, sf, bc);
+        if (mu == 3) wilson_hop_h<3>(acc, u, l, U, false, sf, bc);
+      } else {
+        T psi[24];
+        bc = load_hop_spinor<PREC, T>(src, Vh, cb_index(g, y), psi, bc);
+        Link<T> U;
+        LinkIO<PREC, R>::load(a.gauge, Vh, mu, par, cb, U);
+        if (mu == 0) wilson_hop<0>(acc, psi, U, false, sf, bc);
+        if (mu == 1) wilson_hop<1>(acc, psi, U, false, sf, bc);
+        if (mu == 2) wilson_hop<2>(acc, psi, U, false, sf, bc);
+        if (mu == 3) wilson_hop<3>(acc, psi, U, false, sf, bc);
+      }
     }
     // backward neighbour x - mu, link U_mu(x - mu) stored at (mu, 1 - par, cb(x - mu))
     {
@@ -237,19 +390,48 @@ __device__ __forceinline__ void wilson_site(const WilsonArg& a, int idx) {
         if (mu == 3 && g.apbc) bc = -1;
       }
       int ycb = cb_index(g, y);
-      T psi[24];
-      bc = load_hop_spinor<PREC, T>(src, Vh, ycb, psi, bc);
-      Link<T> U;
-      LinkIO<PREC, R>::load(a.gauge, Vh, mu, 1 - par, ycb, U);
-      if (mu == 0) wilson_hop<0>(acc, psi, U, true, sb, bc);
-      if (mu == 1) wilson_hop<1>(acc, psi, U, true, sb, bc);
-      if (mu == 2) wilson_hop<2>(acc, psi, U, true, sb, bc);
-      if (mu == 3) wilson_hop<3>(acc, psi, U, true, sb, bc);
+      if constexpr (PREC == P16) {
+        float u[12];
+        uint32_t l[6];
+        bc = load_hop_h(src, Vh, ycb, u, l, bc);
+        Link<T> U;
+        LinkIO<PREC, R>::load(a.gauge, Vh, mu, 1 - par, ycb, U);
+        if (mu == 0) wilson_hop_h<0>(acc, u, l, U, true, sb, bc);
+        if (mu == 1) wilson_hop_h<1>(acc, u, l, U, true, sb, bc);
+        if (mu == 2) wilson_hop_h<2>(acc, u, l, U, true, sb, bc);
+        if (mu == 3) wilson_hop_h<3>(acc, u, l, U, true, sb, bc);
+      } else {
+        T psi[24];
+        bc = load_hop_spinor<PREC, T>(src, Vh, ycb, psi, bc);
+        Link<T> U;
+        LinkIO<PREC, R>::load(a.gauge, Vh, mu, 1 - par, ycb, U);
+        if (mu == 0) wilson_hop<0>(acc, psi, U, true, sb, bc);
+        if (mu == 1) wilson_hop<1>(acc, psi, U, true, sb, bc);
+        if (mu == 2) wilson_hop<2>(acc, psi, U, true, sb, bc);
+        if (mu == 3) wilson_hop<3>(acc, psi, U, true, sb, bc);
+      }
     }
   }
 
   T out[24];
-  if (FULLM) {
+  bool clover_done = false;
+  if constexpr (FULLM && PREC == P16) {
+    if (a.clover) {  // Ahat self from the stored binary16 values (no conversions)
+      C<float> av[12];
+      clover_self_h(a.clover + (size_t)par * CloverIO<P16>::parity_bytes(Vh), self_in, Vh, cb, av);
+      const float mk = -(float)a.kappa;
+#pragma unroll
+      for (int s = 0; s < 4; ++s)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          out[6 * s + 2 * c] = fmaf(mk, acc[s][c].r, av[3 * s + c].r);
+          out[6 * s + 2 * c + 1] = fmaf(mk, acc[s][c].i, av[3 * s + c].i);
+        }
+      clover_done = true;
+    }
+  }
+  if (clover_done) {
+  } else if (FULLM) {
     T self[24];
     C<T> sv[12], av[12];
     SpinorIO<PREC, 24>::load(self_in, Vh, cb, self);
