@@ -460,16 +460,26 @@ __device__ __forceinline__ void wilson_site(const WilsonArg& a, int idx) {
       for (int c = 0; c < 3; ++c) v[3 * s + c] = sc * acc[s][c];
     const size_t pb = CloverIO<PREC>::parity_bytes(Vh);
     if (a.self) {
-      T sl[24];
-      SpinorIO<PREC, 24>::load(a.self, Vh, cb, sl);
-      C<T> sv[12], cv[12];
+      C<T> cv[12];
+      bool done = false;
+      if constexpr (PREC == P16) {
+        if (a.c_self) {  // Cself self from the stored binary16 values
+          clover_self_h(a.c_self + par * pb, a.self, Vh, cb, cv);
+          done = true;
+        }
+      }
+      if (!done) {
+        T sl[24];
+        SpinorIO<PREC, 24>::load(a.self, Vh, cb, sl);
+        C<T> sv[12];
 #pragma unroll
-      for (int k = 0; k < 12; ++k) sv[k] = C<T>{sl[2 * k], sl[2 * k + 1]};
-      if (a.c_self) {
-        apply_clover_site<PREC, T>(a.c_self + par * pb, Vh, cb, sv, cv);
-      } else {
+        for (int k = 0; k < 12; ++k) sv[k] = C<T>{sl[2 * k], sl[2 * k + 1]};
+        if (a.c_self) {
+          apply_clover_site<PREC, T>(a.c_self + par * pb, Vh, cb, sv, cv);
+        } else {
 #pragma unroll
-        for (int k = 0; k < 12; ++k) cv[k] = sv[k];
+          for (int k = 0; k < 12; ++k) cv[k] = sv[k];
+        }
       }
 #pragma unroll
       for (int k = 0; k < 12; ++k) v[k] = v[k] + cv[k];
