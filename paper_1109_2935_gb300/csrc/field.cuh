@@ -86,6 +86,20 @@ __device__ __forceinline__ void su3_mv_dag(const Link<T>& U, const C<T> h[3], C<
   }
 }
 
+// fma of one binary16 half of word a and one of word b into an FP32 accumulator: the two
+// binary16 factors enter the fused multiply-add exactly (their product is exact in FP32),
+// so this equals converting both and one FP32 fma, without the conversions.
+template <int HA, int HB>
+__device__ __forceinline__ float fma_hh(uint32_t a, uint32_t b, float c) {
+  float d;
+  asm("{\n\t.reg .b16 a0, a1, b0, b1;\n\t"
+      "mov.b32 {a0, a1}, %1;\n\t"
+      "mov.b32 {b0, b1}, %2;\n\t"
+      "fma.rn.f32.f16 %0, a%4, b%5, %3;\n\t}"
+      : "=f"(d) : "r"(a), "r"(b), "f"(c), "n"(HA), "n"(HB));
+  return d;
+}
+
 // ---------------------------------------------------------------- raw chunk I/O
 template <typename V> __device__ __forceinline__ V ldg_chunk(const char* p) {
   return __ldg(reinterpret_cast<const V*>(p));

@@ -159,20 +159,6 @@ __device__ __forceinline__ void apply_clover_site(const char* b, int Vh, int cb,
 }
 
 // ---------------------------------------------------------------- 16-bit Ahat x self
-// fma of one binary16 half of word a and one of word b into an FP32 accumulator: the two
-// binary16 factors enter the fused multiply-add exactly (their product is exact in FP32),
-// so this equals converting both and one FP32 fma, without the conversions.
-template <int HA, int HB>
-__device__ __forceinline__ float fma_hh(uint32_t a, uint32_t b, float c) {
-  float d;
-  asm("{\n\t.reg .b16 a0, a1, b0, b1;\n\t"
-      "mov.b32 {a0, a1}, %1;\n\t"
-      "mov.b32 {b0, b1}, %2;\n\t"
-      "fma.rn.f32.f16 %0, a%4, b%5, %3;\n\t}"
-      : "=f"(d) : "r"(a), "r"(b), "f"(c), "n"(HA), "n"(HB));
-  return d;
-}
-
 // y = A x for one chirality block with the stored binary16 values of both: blk = the
 // block's 18 half2 words (6 real diagonal entries in words 0..2, then L_ij, i > j, one
 // complex per word), x = 6 complex binary16 words (re low, im high).
