@@ -296,7 +296,7 @@ int batch_create(dirac_ctx* const* ctxs, int nlat, void* const* out, const void*
       b->cand_ms.push_back(-1);
       continue;
     }
-    if (tune == 0) {  // no timing at all
+    if (tune <= 0) {  // no timing at all
       best = 0;
       bi = k;
       b->cand_ms.push_back(-1);
@@ -338,7 +338,7 @@ int batch_create(dirac_ctx* const* ctxs, int nlat, void* const* out, const void*
   b->cc_ms = best;
   // the tensor-core kernel (FP16 storage, 12- or 18-real links): timed the same way; the
   // plan keeps whichever kernel is faster
-  if (prec == DIRAC_PREC_F16 && (recon == 12 || recon == 18)) {
+  if (prec == DIRAC_PREC_F16 && (recon == 12 || recon == 18) && tune >= 0) {
     std::vector<TcLat> tl(nlat);
     int begin = 0;
     for (int l = 0; l < nlat; ++l) {

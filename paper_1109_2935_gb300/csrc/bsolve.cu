@@ -4,8 +4,8 @@
 // Each right-hand side runs its own BiCGstab (Sec. 3.1) with reliable updates (Sec. 8.2:
 // the Krylov space and the operator in a sloppy precision, the solution and the true
 // residual r = b - M x in FP64). What is shared is the work of one iteration: the two
-// operator applications go to batched operator plans (dirac_batch_*: with FP16 storage
-// the tensor-core kernel, all right-hand sides of a site in one contraction), the BLAS
+// operator applications go to batched operator plans (dirac_batch_*, the CUDA-core
+// kernel: it skips the systems that are no longer active), the BLAS
 // updates and reductions of all right-hand sides are single launches over a segment
 // table, and the scalar algebra is one thread per right-hand side. Scalars stay on the
 // GPU; every iteration is replayed from a CUDA graph (two graphs: the iteration's
@@ -799,10 +799,11 @@ extern "C" int solve_batched(dirac_ctx* const* ctxs, int nlat, void* const* x, c
       xin[l] = R.segs[l].f[VX];
       rout[l] = R.segs[l].f[VR];
     }
-    // the sloppy plans time the tensor-core kernel against the default CUDA-core shape;
-    // the FP64 plan is not timed (its launches are seconds of FP64 arithmetic)
-    int rc = batch_create(ctxs, nlat, pout.data(), (const void* const*)pin.data(), nrhs, sp, R.st, &R.plan_pv, 1);
-    if (!rc) rc = batch_create(ctxs, nlat, sout.data(), (const void* const*)sin.data(), nrhs, sp, R.st, &R.plan_st, 1);
+    // the sloppy plans run the default CUDA-core shape (their masks skip converged systems,
+    // which the tensor-core kernel cannot); none of the plans is timed (the FP64 plan's
+    // launches are seconds of FP64 arithmetic)
+    int rc = batch_create(ctxs, nlat, pout.data(), (const void* const*)pin.data(), nrhs, sp, R.st, &R.plan_pv, -1);
+    if (!rc) rc = batch_create(ctxs, nlat, sout.data(), (const void* const*)sin.data(), nrhs, sp, R.st, &R.plan_st, -1);
     if (!rc) rc = batch_create(ctxs, nlat, rout.data(), (const void* const*)xin.data(), nrhs, P64, R.st, &R.plan_x, 0);
     // the reliable updates' residuals in double-single arithmetic where every lattice
     // allows it (FP64 18-real links) and every context has it switched on

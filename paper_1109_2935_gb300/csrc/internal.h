@@ -148,10 +148,13 @@ int schur_reconstruct(dirac_ctx* c, char* x, const char* b, int prec, cudaStream
 // ---------------------------------------------------------------- batched operator (batch.cu)
 // dirac_batch_create with a tuning level: 2 = every tile shape and the tensor-core kernel
 // timed (the public call), 1 = the default shape timed against the tensor-core kernel,
-// 0 = no timing (default shape; the tensor-core kernel where it exists)
+// 0 = no timing (default shape; the tensor-core kernel where it exists), -1 = no timing and
+// the CUDA-core kernel only (default shape; for plans that will be masked)
 // (ds: FP64 fields, 18-real links, arithmetic in double-single as dirac_apply_ds)
 int batch_create(dirac_ctx* const* ctxs, int nlat, void* const* out, const void* const* in, const int* nrhs,
                  int prec, cudaStream_t stream, dirac_batch** plan, int tune, bool ds = false);
+// skip the right-hand sides whose mask[rhs * stride] is 0 (read at every launch); a masked
+// plan runs the CUDA-core kernel
 int batch_set_mask(dirac_batch* b, const double* mask, int stride, cudaStream_t st);
 
 // ---------------------------------------------------------------- PTC network (ptc.cu)
