@@ -286,9 +286,11 @@ int solve(dirac_ctx* ctx, void* x, const void* b, const dirac_solver_params* par
  * params->use_x0). Every right-hand side runs its own BiCGstab (params->alg must be
  * DIRAC_SOLVER_BICGSTAB) with reliable updates every params->delta in
  * params->prec_sloppy, to params->tol; one iteration of all of them is one batched
- * operator application per BiCGstab operator step (the tensor-core kernel for FP16),
- * single BLAS launches over all right-hand sides and a replayed CUDA graph. A converged
- * right-hand side stops changing while the others continue. stats: one entry per
+ * operator application per BiCGstab operator step (the CUDA-core batched kernel),
+ * single BLAS launches over all right-hand sides and a replayed CUDA graph. A reliable
+ * update recomputes the FP64 residual of the right-hand sides that ask for one only; a
+ * converged right-hand side is skipped by every later launch and stops changing while the
+ * others continue. stats: one entry per
  * right-hand side (lattice-major): its iterations, reliable updates and final FP64 true
  * residual; seconds is the wall time of the whole call. Returns DIRAC_ERR_NOT_CONVERGED
  * (or BREAKDOWN / NONFINITE) if some right-hand side did not reach tol; the others keep
