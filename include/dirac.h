@@ -290,7 +290,8 @@ int solve(dirac_ctx* ctx, void* x, const void* b, const dirac_solver_params* par
  * single BLAS launches over all right-hand sides and a replayed CUDA graph. A reliable
  * update recomputes the FP64 residual of the right-hand sides that ask for one only; a
  * converged right-hand side is skipped by every later launch and stops changing while the
- * others continue. stats: one entry per
+ * others continue; each right-hand side's result (bytes, iterations, reliable updates) is
+ * that of solving it alone. stats: one entry per
  * right-hand side (lattice-major): its iterations, reliable updates and final FP64 true
  * residual; seconds is the wall time of the whole call. Returns DIRAC_ERR_NOT_CONVERGED
  * (or BREAKDOWN / NONFINITE) if some right-hand side did not reach tol; the others keep

@@ -10,11 +10,14 @@
 // table, and the scalar algebra is one thread per right-hand side. Scalars stay on the
 // GPU; every iteration is replayed from a CUDA graph (two graphs: the iteration's
 // launches depend only on the mirror slot). The host reads the per-right-hand-side
-// residual norms one iteration behind from mapped memory and decides reliable updates
+// residual norms one iteration behind from mapped memory (skipping, for a right-hand side
+// just updated, the value of the iteration before its update) and decides reliable updates
 // (taken together, in one set of launches, for the right-hand sides that ask; the others
 // are masked out and keep iterating) and convergence; a converged right-hand side is
 // frozen (masked out of the operator and BLAS launches, so x, the correction and the
-// residual stay as they are) while the others continue.
+// residual stay as they are) while the others continue. Nothing of one right-hand side's
+// arithmetic depends on the others, so each returns the bytes, iterations and reliable
+// updates of solve_batched on it alone.
 #include <chrono>
 #include <cmath>
 #include <string>
@@ -561,7 +564,7 @@ int solve_batched_impl(Run& R, const dirac_solver_params& P, dirac_solver_stats*
   k_gather<<<(n + 63) / 64, 64, 0, R.st>>>(R.scal, n, SC_BB, R.gathered());
   if (cudaStreamSynchronize(R.st) != cudaSuccess) return DIRAC_ERR_CUDA;
   std::vector<double> target(n), rmax(n), rr(n);
-  std::vector<int> active(n, 1), relup(n, 0);
+  std::vector<int> active(n, 1), relup(n, 0), stale(n, 0);
   for (int j = 0; j < n; ++j) R.upd_h()[j] = 1;  // the start covers every right-hand side
   for (int j = 0; j < n; ++j) {
     bb[j] = R.hgathered()[j];
@@ -641,6 +644,10 @@ int solve_batched_impl(Run& R, const dirac_solver_params& P, dirac_solver_stats*
       for (int j = 0; j < n; ++j) {
         R.upd_h()[j] = 0;
         if (!active[j]) continue;
+        if (stale[j]) {  // its previous iteration ran before its reliable update
+          stale[j] = 0;
+          continue;
+        }
         const int fl = (int)m[2 * j + 1];
         if (fl != FL_OK) {
           active[j] = 0;
@@ -668,14 +675,17 @@ int solve_batched_impl(Run& R, const dirac_solver_params& P, dirac_solver_stats*
             if (R.upd_h()[j] == 0) continue;
             rr[j] = R.hgathered()[j];
             relup[j]++;
+            stale[j] = 1;
             if (rr[j] < target[j]) active[j] = 0;
             rmax[j] = rr[j];
             R.active_h()[j] = active[j];
           }
           rc = restart<SP, AP>(R, 0);
+          // the restart kernels read the mapped update and active flags, which the host
+          // rewrites at the next check: they must have run first
+          if (rc == DIRAC_OK && cudaStreamSynchronize(R.st) != cudaSuccess) rc = DIRAC_ERR_CUDA;
         }
         nvtxRangePop();
-        it = -1;
       }
     }
     ++it;

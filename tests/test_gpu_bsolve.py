@@ -95,3 +95,32 @@ def test_batched_initial_guess_and_errors(dirac):
     bs[0][:8] = 255
     res4 = dirac.solve_many(lats, xs, bs, [2, 1], raise_on_error=False)
     assert res4["status"] == "ERR_NONFINITE"
+
+
+@pytest.mark.parametrize("sloppy", [2, 1])
+def test_each_system_as_if_solved_alone(dirac, sloppy):
+    """Batching does not change any system's iterates: every right-hand side, solved
+    together with systems of other lattices that converge and update at other times,
+    returns the bytes and the iteration and reliable-update counts of solve_batched on
+    that right-hand side alone (per-system scalars, reductions, masks and reliable
+    updates; the operator and BLAS per right-hand side do not depend on the others)."""
+    specs = [((4, 4, 4, 6), 0.128, 2), ((6, 4, 4, 8), 0.135, 3)]
+    lats, xs, bs, _ = _problem(dirac, specs)
+    res = dirac.solve_many(lats, xs, bs, [s[2] for s in specs], tol=1e-10, max_iter=2000, delta=0.1,
+                           prec_sloppy=sloppy)
+    assert res["status"] == "OK"
+    iters = [st["iters"] for st in res["rhs"]]
+    assert len(set(iters)) > 1  # the systems really converge at different iterations
+    k = 0
+    for lat, x, b, (dims, kappa, n) in zip(lats, xs, bs, specs):
+        fb = lat.field_bytes(dirac.F64)
+        for r in range(n):
+            x1 = torch.zeros(fb, dtype=torch.uint8, device="cuda")
+            b1 = b[r * fb:(r + 1) * fb].clone()
+            one = dirac.solve_many([lat], [x1], [b1], [1], tol=1e-10, max_iter=2000, delta=0.1,
+                                   prec_sloppy=sloppy)
+            assert one["status"] == "OK"
+            assert one["rhs"][0]["iters"] == res["rhs"][k]["iters"], (k, one["rhs"][0], res["rhs"][k])
+            assert one["rhs"][0]["reliable_updates"] == res["rhs"][k]["reliable_updates"]
+            assert torch.equal(x1, x[r * fb:(r + 1) * fb]), k
+            k += 1
