@@ -189,3 +189,37 @@ def test_rank_grid_halo_exchange_matches_whole_lattice(grid):
     for rank, err, n2, n2_ref in got:
         assert err < 1e-13, (rank, err)
         assert abs(n2 - n2_ref) < 1e-12 * n2_ref
+
+
+def _grid_check_worker(port, q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    from paper_1109_2935_gb300.halo import HaloExchange
+    dist.init_process_group("gloo", rank=0, world_size=1)
+    out = []
+    for grid in ((1, 1, 1, 1), (2, 1, 1, 1), (1, 1, 0, 1), (1, 1, 1)):
+        try:
+            hx = HaloExchange(grid=grid)
+            f = torch.arange(4, dtype=torch.float64)
+            a, b = hx.exchange(f, f + 1, mu=2)   # one rank in z: its own faces, no messages
+            out.append(("ok", hx.coords, bool(torch.equal(a, f) and torch.equal(b, f + 1))))
+        except ValueError:
+            out.append(("ValueError",))
+    dist.destroy_process_group()
+    q.put(out)
+
+
+def test_rank_grid_must_match_the_world():
+    """A grid whose ranks do not multiply to the world size (or has a zero / missing
+    dimension) is rejected; in a dimension with one rank the faces are the rank's own."""
+    port = _free_port()
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    p = ctx.Process(target=_grid_check_worker, args=(port, q))
+    p.start()
+    p.join(120)
+    assert p.exitcode == 0
+    out = q.get(timeout=10)
+    assert out[0] == ("ok", (0, 0, 0, 0), True)
+    assert out[1:] == [("ValueError",)] * 3
