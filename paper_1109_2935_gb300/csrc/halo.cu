@@ -197,7 +197,9 @@ struct DDArg {
 };
 
 // M (or M^dagger) at one local site, the operation order of wilson_site<PREC,R,true>.
-template <int PREC, int R>
+// CUT >= 0: the cut dimensions as a compile-time bit mask (bit mu), so that the ghost
+// branches of whole dimensions are compiled out; CUT < 0: read from a.cut.
+template <int PREC, int R, int CUT>
 __global__ void __launch_bounds__(WilsonShape<PREC>::threads, WilsonShape<PREC>::minb) dd_wilson_kernel(const DDArg a) {
   using T = typename Real<PREC>::T;
   const Geom& g = a.g;
@@ -228,7 +230,8 @@ __global__ void __launch_bounds__(WilsonShape<PREC>::threads, WilsonShape<PREC>:
       T bc = 1;
       Link<T> U;
       LinkIO<PREC, R>::load(a.gauge, Vh, mu, par, cb, U);
-      if (a.cut[mu] && x[mu] == g.L[mu] - 1) {
+      const bool cut = CUT >= 0 ? ((CUT >> mu) & 1) != 0 : a.cut[mu] != 0;
+      if (cut && x[mu] == g.L[mu] - 1) {
         const T* h = reinterpret_cast<const T*>(a.ghost_fwd[mu] + (size_t)face_index(g, x, mu) * Face<PREC>::site_bytes);
 #pragma unroll
         for (int k = 0; k < 12; ++k) { psi[k] = h[k]; psi[12 + k] = 0; }
@@ -251,7 +254,8 @@ __global__ void __launch_bounds__(WilsonShape<PREC>::threads, WilsonShape<PREC>:
       T psi[24];
       T bc = 1;
       Link<T> U;
-      if (a.cut[mu] && x[mu] == 0) {
+      const bool cut = CUT >= 0 ? ((CUT >> mu) & 1) != 0 : a.cut[mu] != 0;
+      if (cut && x[mu] == 0) {
         const int fi = face_index(g, x, mu);
         const T* h = reinterpret_cast<const T*>(a.ghost_bwd[mu] + (size_t)fi * Face<PREC>::site_bytes);
 #pragma unroll
@@ -296,15 +300,23 @@ __global__ void __launch_bounds__(WilsonShape<PREC>::threads, WilsonShape<PREC>:
   SpinorIO<PREC, 24>::store(a.out + (size_t)par * hb, Vh, cb, out);
 }
 
+template <int PREC, int CUT>
+void launch_dd_cut(int recon, const DDArg& a, dim3 grid, cudaStream_t st) {
+  constexpr int T = WilsonShape<PREC>::threads;  // the single-domain kernel's launch shape
+  if (recon == 18) dd_wilson_kernel<PREC, 18, CUT><<<grid, T, 0, st>>>(a);
+  else if (recon == 12) dd_wilson_kernel<PREC, 12, CUT><<<grid, T, 0, st>>>(a);
+  else dd_wilson_kernel<PREC, 8, CUT><<<grid, T, 0, st>>>(a);
+}
+
 template <int PREC>
 void launch_dd(int recon, const DDArg& a, cudaStream_t st) {
   const long n = (long)a.n[0] * a.n[1] * a.n[2] * a.n[3];
   if (n <= 0) return;
-  constexpr int T = WilsonShape<PREC>::threads;  // the single-domain kernel's launch shape
+  constexpr int T = WilsonShape<PREC>::threads;
   dim3 grid((unsigned)((n + T - 1) / T));
-  if (recon == 18) dd_wilson_kernel<PREC, 18><<<grid, T, 0, st>>>(a);
-  else if (recon == 12) dd_wilson_kernel<PREC, 12><<<grid, T, 0, st>>>(a);
-  else dd_wilson_kernel<PREC, 8><<<grid, T, 0, st>>>(a);
+  const bool t_only = !a.cut[0] && !a.cut[1] && !a.cut[2] && a.cut[3];
+  if (t_only) launch_dd_cut<PREC, 8>(recon, a, grid, st);  // t-slabs, the common case
+  else launch_dd_cut<PREC, -1>(recon, a, grid, st);
 }
 
 void launch_dd_any(int prec, int recon, const DDArg& a, cudaStream_t st) {
